@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the snapshot path on one GB300 (or N replicas).
+
+One step = one pass of the whole path over the llama.cpp-shaped synthetic
+snapshot (400 regions, ~0.39 GiB, 64 KiB pages) and its fp32 logits pairs:
+  kc_scan    fused XXH64 page digest + zero flags + pointer census
+  kc_dedup   radix sort, byte verification, page table, blob pack
+  kc_restore blobs written back at their VA offsets (in place: the regions
+             are rewritten with identical bytes, so every step sees the same
+             input)
+  kc_compare fp32 [8, 32000] x 2 pairs, FP64 error maxima
+value = algorithmic bytes of the step / device time of the step:
+  2N (scan read + restore write) + 3U (pack read/write, restore read, U =
+  unique non-zero page bytes) + 2C (compare read).
+Inputs (0.39 GiB) are larger than the 129 MB L2, so no flush is needed.
+
+--impl reference times the CPU oracle (oracle/kc_oracle.c, single-threaded)
+on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GB/s & % HBM peak for digest+dedup+census+compare; batched vs plain; p99 ms"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="kc", choices=["kc", "reference"])
+    ap.add_argument("--variant", default="full", choices=["full", "152MB"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the GPU works."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        inside = [r for r in rows if t0 - 0.25 <= r[0] <= t1 + 0.25] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in inside for n, v in zip(names, r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in rows), "reasons": reasons,
+                "samples": len(inside)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(seed: int, variant: str, device: str):
+    import torch
+    from paper_2605_03208_gb300 import workloads as W
+    layout = W.llama_layout(seed, variant=variant)
+    dev = [torch.empty(int(s), dtype=torch.uint8, device=device) for s in layout.sizes]
+    snap = W.llama_fill(layout, [t.data_ptr() for t in dev], seed)
+    for t, r in zip(dev, snap.regions):
+        t.copy_(torch.from_numpy(r), non_blocking=False)
+    pairs = W.llama_pairs(seed)
+    return snap, dev, pairs
+
+
+class KcStep:
+    """Outputs and the call sequence of one step through the C ABI."""
+
+    def __init__(self, ctx, snap, dev, pairs, device):
+        import torch
+        from paper_2605_03208_gb300 import kc
+        from paper_2605_03208_gb300 import workloads as W
+        self.kc, self.ctx, self.snap, self.dev = kc, ctx, snap, dev
+        self.S = snap.page_bytes
+        self.b = kc.bufs([(t.data_ptr(), t.numel(), dt, 0) for t, dt in zip(dev, snap.dtypes)])
+        self.P = kc.page_count(self.b, self.S)
+        self.win = W.default_window(snap.bases, snap.sizes)
+        self.cap = 1 << 16
+        mk = lambda n, dt=torch.uint8: torch.empty(n, dtype=dt, device=device)  # noqa: E731
+        self.hash = mk(self.P, torch.int64)
+        self.zero = mk(self.P)
+        self.pf = mk(len(dev) + 1, torch.int64)
+        self.hits = mk(self.cap * 24)
+        self.counts = torch.zeros(2, dtype=torch.int64, device=device)
+        self.table = mk(self.P * 16)
+        self.arena = mk(self.P * self.S)
+        self.nblobs = torch.zeros(1, dtype=torch.int64, device=device)
+        self.g = [torch.from_numpy(p.got.view(np.uint8)).to(device) for p in pairs]
+        self.w = [torch.from_numpy(p.want.view(np.uint8)).to(device) for p in pairs]
+        self.gb = kc.bufs([(x.data_ptr(), x.numel(), p.dtype, 0) for x, p in zip(self.g, pairs)])
+        self.wb = kc.bufs([(x.data_ptr(), x.numel(), p.dtype, 0) for x, p in zip(self.w, pairs)])
+        self.cmp = mk(len(pairs) * 64)
+        self.N = sum(int(s) for s in snap.sizes)
+        self.C = sum(x.numel() for x in self.g)
+
+    def run(self, stream, trace=None):
+        """Enqueue one step.  trace: dict op -> (start, stop) events for main kernels."""
+        ctx, S = self.ctx, self.S
+        t = trace or {}
+        if "scan" in t:
+            ctx.set_trace_events(*t["scan"])
+        ctx.scan(self.b, S, self.hash, self.zero, self.pf, self.win[0], self.win[1], self.hits,
+                 self.cap, self.counts, stream)
+        if "dedup" in t:
+            ctx.set_trace_events(*t["dedup"])
+        ctx.dedup(self.b, S, self.hash, self.zero, self.table, self.arena, self.P * S, self.nblobs,
+                  stream)
+        if "restore" in t:
+            ctx.set_trace_events(*t["restore"])
+        ctx.restore(self.b, S, self.table, self.P, self.arena, self.P * S, stream)
+        if "compare" in t:
+            ctx.set_trace_events(*t["compare"])
+        ctx.compare(self.gb, self.wb, 0.0, 0.0, self.cmp, stream)
+        if t:
+            ctx.set_trace_events(None, None)
+
+    def unique_bytes(self):
+        nb = int(self.nblobs.cpu().numpy().view(np.uint64)[0])
+        tbl = self.table.cpu().numpy().view(self.kc.PAGE_DTYPE)
+        # bytes of the canonical pages (blob slots hold S bytes, the page may be shorter)
+        lens = []
+        seen = set()
+        sizes = self.snap.sizes
+        for row in tbl:
+            b = int(row["blob"])
+            if b >= 0xFFFFFFFE or b in seen:
+                continue
+            seen.add(b)
+            lens.append(min(self.S, int(sizes[int(row["alloc_id"])]) - int(row["va_offset"])))
+        return nb, int(sum(lens))
+
+
+def algorithmic_bytes(N, U, C, P, pairs):
+    return {"scan": N + 9 * P, "dedup": 2 * U, "restore": U + N, "compare": C + 64 * pairs}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+
+def oracle_step(snap, pairs, sample_regions=None):
+    """One pass of the oracle over (a sample of) the workload; returns bytes-defined units."""
+    import oracle
+    from paper_2605_03208_gb300 import workloads as W
+    idx = list(range(len(snap.sizes))) if sample_regions is None else sample_regions
+    regions = [snap.regions[i] for i in idx]
+    bases = [snap.bases[i] for i in idx]
+    S = snap.page_bytes
+    win = W.default_window(snap.bases, snap.sizes)
+    h, z, pf = oracle.digest(regions, S)
+    oracle.census(regions, bases, *win)
+    t = oracle.dedup(regions, S, h, z)
+    arena = oracle.pack(regions, S, t)
+    targets = [np.empty_like(r) for r in regions]
+    oracle.restore(targets, S, t, arena)
+    for p in pairs:
+        oracle.compare(p.got, p.want, p.dtype)
+    N = sum(r.size for r in regions)
+    U = 0
+    for p in range(len(t["blob"])):
+        if t["blob"][p] != oracle.BLOB_ZERO and t["canon"][p] == p:
+            a = int(t["alloc"][p])
+            U += min(S, regions[a].size - int(t["off"][p]))
+    C = sum(p.got.nbytes + p.want.nbytes for p in pairs)
+    ab = algorithmic_bytes(N, U, C, len(h), len(pairs))
+    return sum(ab.values()), N
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2605_03208_gb300 import workloads as W
+    layout = W.llama_layout(args.seed, variant=args.variant)
+    snap = W.llama_fill(layout, W.fake_bases(layout.sizes, args.seed), args.seed)
+    pairs = W.llama_pairs(args.seed)
+    # size the per-step sample so the whole run ends within ~3 minutes
+    t0 = time.perf_counter()
+    oracle_step(snap, pairs, sample_regions=list(range(0, len(snap.sizes), 8)))
+    t_probe = (time.perf_counter() - t0) * 8
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    frac = min(1.0, budget / max(t_probe, 1e-6))
+    stride = max(1, int(round(1.0 / frac)))
+    sample = list(range(0, len(snap.sizes), stride))
+    for _ in range(args.warmup):
+        oracle_step(snap, pairs, sample)
+    times, abytes = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        abytes, Nsamp = oracle_step(snap, pairs, sample)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = abytes / (ms / 1000) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": snap.name, "regions": len(snap.sizes),
+                       "snapshot_bytes": snap.total_bytes, "page_bytes": snap.page_bytes,
+                       "compare": "fp32 [8,32000] x 2 pairs"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"every {stride}th region ({len(sample)} of "
+                                       f"{len(snap.sizes)}, {Nsamp} bytes) + both compare pairs"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+def run_kc(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2605_03208_gb300 import kc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    kc.load()
+    ctx = kc.Context(local)
+    snap, dev, pairs = make_workload(args.seed + rank, args.variant, device)
+    step = KcStep(ctx, snap, dev, pairs, device)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (also sizes the context's scratch)
+    for _ in range(max(args.warmup, 3)):
+        step.run(stream)
+    st = ctx.sync(stream)
+    if st != kc.OK:
+        raise RuntimeError(f"device status after warm-up: {kc.status_name(st)}")
+    nblobs, U = step.unique_bytes()
+    ab = algorithmic_bytes(step.N, U, step.C, step.P, len(pairs))
+    step_bytes = sum(ab.values())
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    # ---- timed region: exactly K steps, device time with CUDA events
+    ops = ["scan", "dedup", "restore", "compare"]
+    tr = {op: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)] for op in ops}
+    barrier()
+    launches0 = kc.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    for i in range(args.steps):
+        step.run(stream, {op: tr[op][i] for op in ops})
+    e1.record(stream)
+    barrier()
+    t_wall1 = time.time()
+    launches = kc.launch_count() - launches0
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    op_ms = {op: statistics.mean(a.elapsed_time(b) for a, b in tr[op]) for op in ops}
+    time.sleep(0.3)
+    sampler.stop()
+    st = ctx.sync(stream)
+    if st != kc.OK:
+        raise RuntimeError(f"device status after timed steps: {kc.status_name(st)}")
+
+    # ---- end to end: pinned host inputs copied in, results read back, every step
+    host_regions = [torch.from_numpy(r).pin_memory() for r in snap.regions]
+    host_g = [x.cpu().pin_memory() for x in step.g]
+    host_w = [x.cpu().pin_memory() for x in step.w]
+    outs = [step.hash, step.zero, step.counts, step.table, step.nblobs, step.cmp]
+    host_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+    h2d = sum(r.numel() for r in host_regions) + sum(x.numel() for x in host_g + host_w)
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    k_e2e = max(3, min(args.steps, 50))
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(k_e2e):
+        for d, h in zip(dev, host_regions):
+            d.copy_(h, non_blocking=True)
+        for d, h in zip(step.g + step.w, host_g + host_w):
+            d.copy_(h, non_blocking=True)
+        step.run(stream)
+        for h, o in zip(host_out, outs):
+            h.copy_(o, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1) / k_e2e
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    peak, peak_kind = peaks()
+    value = world * step_bytes / (ms / 1000) / 1e9
+    scan_bytes = ab["scan"]
+    achieved = scan_bytes / (op_ms["scan"] / 1000) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": snap.name, "regions": len(snap.sizes), "snapshot_bytes": step.N,
+                   "pages": step.P, "page_bytes": step.S, "unique_bytes": U, "blobs": nblobs,
+                   "compare": "fp32 [8,32000] x 2 pairs", "parallelism": f"replicas{world}",
+                   "l2": "inputs (0.39 GiB) larger than L2; no flush",
+                   "step": "scan(digest+census) + dedup(+pack) + restore + compare"},
+        "hbm_frac": value / world / peak,
+        "roofline": {"bound": "hbm", "kernel": "digest_kernel<census> (kc_scan)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes": scan_bytes},
+        "ops": {op: {"ms": op_ms[op], "GB/s": ab[op] / (op_ms[op] / 1000) / 1e9,
+                     "frac": ab[op] / (op_ms[op] / 1000) / 1e9 / peak,
+                     "algorithmic_bytes": ab[op]} for op in ops},
+        "e2e": {"value": world * step_bytes / (e2e_ms / 1000) / 1e9, "unit": "GB/s",
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": sampler.summary(t_wall0, t_wall1),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        sample = list(range(len(snap.sizes)))
+        ob, _ = oracle_step(snap, pairs, sample)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ob / dt / 1e9, "unit": "GB/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "one full step of the same workload (all 400 regions,"
+                                          " both pairs), single thread"}
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_kc(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

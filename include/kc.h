@@ -1,0 +1,275 @@
+/*
+ * kc.h -- C ABI of the GB300 snapshot library: page digest, page dedup,
+ * embedded-pointer census, VA-faithful restore and per-dtype comparison of
+ * captured device memory.
+ *
+ * The operations follow the data path of address-space-closure capture and
+ * replay validation (Kerncap):
+ *   - a snapshot covers every tracked device region, streamed in fixed-size
+ *     chunks (Section "Memory Capture", HIP path: VA-faithful device memory
+ *     snapshot);
+ *   - capturing every region at its original VA captures embedded pointers,
+ *     and pointers escaping the captured set break the closure (same
+ *     section, paragraphs "Handling embedded device pointers via
+ *     address-space closure" and "Bounds of the closure");
+ *   - replay copies the captured data back into each region at the same VA
+ *     (Section "VA-Faithful HSA Replay", stage 5);
+ *   - validation compares replayed outputs byte-exactly or with
+ *     numpy.allclose-style tolerances and reports NaNs explicitly (Section
+ *     "Replay Validation");
+ *   - a region freed before its copy is a per-region failure that must not
+ *     corrupt the other regions' results (Section "Memory Capture",
+ *     paragraph "Ordering and crash safety"; Section "Limitations", memory
+ *     snapshot fragility).
+ * The paper copies regions verbatim; hashing pages with XXH64 (seed 0,
+ * public xxHash specification), deduplicating them and classifying pointers
+ * word by word are this library's GPU formulation of that snapshot.
+ *
+ * Conventions for every call:
+ *   - `d_` pointers are device pointers owned by the caller; plain pointers
+ *     are host pointers read during the call only.  kc_buf.base_va names a
+ *     device VA of the context's device.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) and return after enqueueing; the host-side return
+ *     value reports argument errors and launch failures.  Conditions only
+ *     the GPU can see (truncation, a wait that timed out, a malformed page
+ *     table row) are accumulated in the context and returned by kc_sync().
+ *   - A context serves one stream at a time: two calls on one context that
+ *     may overlap on the GPU (different streams without ordering) race on
+ *     the context's scratch.  Use one context per stream.
+ *   - Region bases must be 16-byte aligned; sizes must be > 0.  No call
+ *     aborts the process or traps on the device.
+ *   - Page sizes are powers of two in [4 KiB, 2 MiB].
+ */
+#ifndef KC_H
+#define KC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KC_VERSION 1
+
+#if defined(__GNUC__)
+#define KC_API __attribute__((visibility("default")))
+#else
+#define KC_API
+#endif
+
+/* Element type of a buffer; only kc_compare interprets it. */
+typedef enum {
+    KC_U8 = 0,   /* uint8: also the byte-exact diff of the validation section */
+    KC_I32 = 1,  /* int32 */
+    KC_F16 = 2,  /* IEEE binary16 */
+    KC_BF16 = 3, /* bfloat16 */
+    KC_F32 = 4,  /* IEEE binary32 */
+    KC_RAW = 5   /* opaque bytes; compared as uint8 */
+} kc_dtype;
+
+typedef enum {
+    KC_OK = 0,
+    KC_EINVAL = 1,   /* bad argument (size, alignment, dtype, page size, table row) */
+    KC_EOVERLAP = 2, /* two regions' VA ranges overlap */
+    KC_ENOMEM = 3,   /* scratch allocation failed, or would be needed inside a
+                        stream capture */
+    KC_ETRUNC = 4,   /* an output was too small; true counts were still written */
+    KC_ECUDA = 5,    /* a CUDA runtime call failed; see kc_last_error */
+    KC_ETIMEOUT = 6, /* a bounded device wait gave up; the affected outputs are stale */
+    KC_EBUF = 7      /* one or more regions could not be read (see kc_buf_status);
+                        the other regions' results are complete */
+} kc_status;
+
+/* kc_buf.flags */
+#define KC_BUF_LOST 0x1 /* the region could not be captured (e.g. freed before
+                           its copy): skip it, mark its outputs, report KC_EBUF */
+
+/* One captured region: [base_va, base_va + bytes) on the context's device. */
+typedef struct {
+    uint64_t base_va;
+    uint64_t bytes;
+    int32_t dtype; /* kc_dtype */
+    int32_t flags; /* KC_BUF_* */
+} kc_buf;
+
+/* zero[] values written by kc_digest */
+#define KC_PAGE_DATA 0 /* page holds a non-zero byte */
+#define KC_PAGE_ZERO 1 /* every byte of the page is 0 */
+#define KC_PAGE_LOST 2 /* region was not readable; hash is 0 */
+
+/* One row of the VA-faithful page table (16 bytes). */
+typedef struct {
+    uint64_t va_offset; /* byte offset of the page inside its region (j * page_bytes) */
+    uint32_t alloc_id;  /* index of the region in the caller's kc_buf list */
+    uint32_t blob;      /* arena slot, or KC_BLOB_ZERO / KC_BLOB_LOST */
+} kc_page;
+
+#define KC_BLOB_ZERO 0xFFFFFFFFu /* all-zero page: restore writes zeros */
+#define KC_BLOB_LOST 0xFFFFFFFEu /* page of a lost region: restore skips it */
+
+/* One embedded pointer found by the census (24 bytes). */
+typedef struct {
+    uint64_t src_offset; /* byte offset of the word inside its source region (multiple of 8) */
+    uint64_t value;      /* the word, little-endian u64 */
+    uint32_t src_alloc;  /* source region's index in the caller's list */
+    int32_t target;      /* index of the region holding `value`, or -1 (outside) */
+} kc_hit;
+
+/* Result of one comparison pair (64 bytes). */
+typedef struct {
+    uint64_t mismatches;   /* elements that are not close (NaN==NaN is close) */
+    int64_t first;         /* smallest mismatching element index, -1 if none */
+    double max_abs;        /* max |got - want| over non-NaN unequal elements (FP64) */
+    double max_rel;        /* max |got - want| / |want| over the same set (+inf if want == 0) */
+    uint64_t nan_got;      /* NaN elements in got */
+    uint64_t nan_want;     /* NaN elements in want */
+    uint64_t nan_mismatch; /* elements where exactly one side is NaN */
+    int32_t status;        /* KC_OK, or KC_EBUF if either buffer was lost */
+    uint32_t reserved;
+} kc_cmp_result;
+
+typedef struct kc_ctx kc_ctx;
+
+/* ---- context --------------------------------------------------------------
+ * kc_create: make a context on CUDA device `device`.  The context owns
+ * device scratch (sort buffers, counters, region tables) that grows on
+ * demand; growth is refused inside a stream capture (KC_ENOMEM), so make one
+ * uncaptured call of each shape first.  Returns KC_OK, KC_EINVAL (null out,
+ * bad device) or KC_ECUDA.
+ * kc_destroy: release everything (waits for the context's work to finish).
+ * kc_last_error: human-readable reason of the last failing call (owned by
+ * the context, valid until the next call).
+ */
+KC_API kc_status kc_create(kc_ctx **out, int device);
+KC_API void kc_destroy(kc_ctx *ctx);
+KC_API const char *kc_last_error(const kc_ctx *ctx);
+KC_API const char *kc_status_name(int status);
+KC_API int kc_version(void);
+/* kc_launch_count: number of CUDA kernels this library has launched in this
+ * process so far (all contexts). */
+KC_API uint64_t kc_launch_count(void);
+
+/* kc_sync: wait for `stream`, then return (and clear) the worst device-side
+ * condition raised by the context's kernels since the previous kc_sync:
+ * KC_ETIMEOUT > KC_EINVAL (malformed page-table row) > KC_ETRUNC > KC_OK. */
+KC_API kc_status kc_sync(kc_ctx *ctx, void *stream);
+
+/* kc_buf_status: status of region `i` in the context's last call that took
+ * a region list (KC_OK, or KC_EBUF when it was lost).  -1 if out of range. */
+KC_API int kc_buf_status(const kc_ctx *ctx, int i);
+
+/* kc_set_digest_shape: pin the digest kernel's launch shape for this
+ * context: `warps` per CTA (1..16), ring `stages` per warp (2..8), `chunk`
+ * bytes per page per stage (multiple of 128, 256..8192).  All three 0
+ * restores the built-in choice.  The shape changes speed only, never
+ * results.  KC_EINVAL if out of range.
+ * kc_get_digest_shape: the shape a digest of `npages` pages of
+ * `page_bytes` would use now, and its grid size (`ctas`). */
+KC_API kc_status kc_set_digest_shape(kc_ctx *ctx, int warps, int stages, int chunk);
+KC_API kc_status kc_get_digest_shape(kc_ctx *ctx, uint32_t page_bytes, uint64_t npages, int *warps,
+                                     int *stages, int *chunk, int *ctas);
+
+/* kc_set_trace_events: `start` and `stop` (cudaEvent_t, or NULL to turn
+ * tracing off) are recorded on the call's stream around the main kernel of
+ * every following call: the digest kernel of kc_digest / kc_scan, the count
+ * kernel of kc_census, the whole pipeline of kc_dedup, the restore kernel,
+ * the compare kernels.  Timing them with cudaEventElapsedTime measures that
+ * kernel alone.  The events stay owned by the caller. */
+KC_API kc_status kc_set_trace_events(kc_ctx *ctx, void *start, void *stop);
+
+/* kc_page_count: number of pages of `n` regions at `page_bytes` per page
+ * (the last page of each region is partial).  Host only. */
+KC_API uint64_t kc_page_count(const kc_buf *bufs, int n, uint32_t page_bytes);
+
+/* ---- digest ---------------------------------------------------------------
+ * For region i (list order) and page j = 0 .. ceil(bytes_i / S) - 1:
+ *   d_hash[p] = XXH64(seed 0) of bytes [jS, min((j+1)S, bytes_i)), unpadded;
+ *   d_zero[p] = KC_PAGE_ZERO if every one of those bytes is 0, else
+ *               KC_PAGE_DATA (KC_PAGE_LOST, hash 0, for a lost region),
+ * with p = d_page_first[i] + j; d_page_first has n + 1 entries, the last
+ * being the page count P.  d_hash: P u64; d_zero: P u8.
+ * Errors: KC_EINVAL (n < 1, null output, page size, alignment, empty
+ * region), KC_ECUDA, KC_EBUF (other regions complete).
+ */
+KC_API kc_status kc_digest(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page_bytes,
+                    uint64_t *d_hash, uint8_t *d_zero, uint64_t *d_page_first, void *stream);
+
+/* ---- census ---------------------------------------------------------------
+ * For every region i (list order) and every offset o = 0, 8, ... with
+ * o + 8 <= bytes_i, the little-endian u64 word v at base_i + o is
+ *   INSIDE  (target k) if base_k <= v < base_k + bytes_k for some region k,
+ *   OUTSIDE (target -1) otherwise, if win_lo <= v < win_hi,
+ *   not a hit otherwise.
+ * Regions are half-open VA ranges and must not overlap (KC_EOVERLAP).  Hits
+ * are written to d_hits in (region, offset) order, at most `cap` of them;
+ * d_counts (device, 2 x u64) receives {n_inside, n_outside}, the true
+ * counts even when they exceed cap (kc_sync then reports KC_ETRUNC).
+ * d_hits may be NULL with cap 0 to count only.  A lost region is not
+ * scanned but stays a target.
+ */
+KC_API kc_status kc_census(kc_ctx *ctx, const kc_buf *allocs, int n, uint64_t win_lo, uint64_t win_hi,
+                    kc_hit *d_hits, uint64_t cap, uint64_t *d_counts, void *stream);
+
+/* kc_scan: kc_digest and kc_census fused into one read of the snapshot
+ * (the census is counted while pages are hashed, then only pages that hold
+ * hits are read a second time to write them in order).  Outputs and errors
+ * are exactly those of the two calls. */
+KC_API kc_status kc_scan(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page_bytes,
+                  uint64_t *d_hash, uint8_t *d_zero, uint64_t *d_page_first,
+                  uint64_t win_lo, uint64_t win_hi, kc_hit *d_hits, uint64_t cap,
+                  uint64_t *d_counts, void *stream);
+
+/* ---- dedup ----------------------------------------------------------------
+ * Input: the digest of the same regions at the same page size (d_hash,
+ * d_zero).  Non-zero pages are grouped by a device radix sort of their
+ * hashes and byte-verified; two pages are duplicates iff they have the same
+ * length and the same bytes.  canonical(p) = the smallest page id of p's
+ * class; blobs are numbered 0, 1, ... in increasing canonical page id.
+ * d_table[p] = {j * S, i, blob(canonical(p))}, KC_BLOB_ZERO for zero pages,
+ * KC_BLOB_LOST for lost pages (P rows).  *d_n_blobs (device u64) = number
+ * of blobs.  If d_arena is not NULL and arena_cap >= n_blobs * S, every
+ * canonical page is packed into d_arena[blob * S ...], zero-filled to S;
+ * if it is too small nothing is packed and kc_sync reports KC_ETRUNC
+ * (d_arena NULL = table only).
+ */
+KC_API kc_status kc_dedup(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page_bytes,
+                   const uint64_t *d_hash, const uint8_t *d_zero, kc_page *d_table,
+                   uint8_t *d_arena, uint64_t arena_cap, uint64_t *d_n_blobs, void *stream);
+
+/* ---- restore --------------------------------------------------------------
+ * For each of the n_pages rows r of d_table: len = min(S, bytes_a - off)
+ * with a = r.alloc_id, off = r.va_offset; write len bytes at base_a + off:
+ * zeros for KC_BLOB_ZERO, nothing for KC_BLOB_LOST, else the bytes
+ * d_arena[r.blob * S ...].  Rows that point outside a region or outside
+ * the arena (arena_bytes) are skipped and reported as KC_EINVAL by kc_sync.
+ * `allocs` gives the restore targets: the captured VAs for a VA-faithful
+ * restore, or explicit new bases (a relocation the caller asks for).
+ */
+KC_API kc_status kc_restore(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page_bytes,
+                     const kc_page *d_table, uint64_t n_pages, const uint8_t *d_arena,
+                     uint64_t arena_bytes, void *stream);
+
+/* ---- compare --------------------------------------------------------------
+ * For pair k, got[k] and want[k] hold the same number of bytes, a multiple
+ * of the element size of got[k].dtype (want[k].dtype is ignored).  Every
+ * element is widened exactly to FP64 (a = got, b = want):
+ *   both NaN -> equal;  one NaN -> mismatch, nan_mismatch++;
+ *   a == b (so +0 == -0) -> equal;
+ *   otherwise d = |a - b|, r = d / |b| (+inf if b == 0 or d is infinite),
+ *   max_abs = max d, max_rel = max r over these elements, and the element
+ *   mismatches if a or b is infinite or d > atol + rtol * |b|.
+ * d_out[k] receives the kc_cmp_result; all FP64 operations are single IEEE
+ * round-to-nearest steps, so results do not depend on the order of work.
+ * Errors: KC_EINVAL (sizes, dtype, alignment to 16 bytes, negative or NaN
+ * tolerance), KC_EBUF (a lost buffer: that pair's status is KC_EBUF).
+ */
+KC_API kc_status kc_compare(kc_ctx *ctx, const kc_buf *got, const kc_buf *want, int npairs,
+                     double atol, double rtol, kc_cmp_result *d_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KC_H */

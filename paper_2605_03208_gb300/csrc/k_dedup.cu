@@ -1,0 +1,663 @@
+// k_dedup.cu -- byte-verified page dedup and blob packing.
+//
+// Pipeline (every count the host cannot know without a sync -- the number of
+// non-zero pages m, of equal-hash neighbours, of bad segments, of blobs --
+// stays in device memory and is read by the kernels themselves):
+//   1. compact the non-zero pages into (hash, page id) pairs, page order;
+//   2. stable LSD radix sort on the 64-bit hash, 8-bit digits, 8 passes:
+//      equal hashes end up adjacent, in increasing page id;
+//   3. segments = runs of equal hash; every element that has an equal-hash
+//      predecessor is byte-compared with it (16 KiB pieces, one warp each);
+//   4. a segment whose elements all equal their predecessors is one class,
+//      canonical = its first (smallest) page id; any other segment (a hash
+//      collision, or equal hashes of different lengths) takes the slow path:
+//      one CTA visits its pages in order and compares each with the
+//      representatives found so far, exactly the class definition;
+//   5. blob ids = exclusive scan of "page is canonical" in page order; the
+//      page table is written VA-faithfully (region index, offset);
+//   6. pack copies every canonical page into its arena slot, zero-filled.
+#include <cuda_runtime.h>
+
+#include "kc_device.cuh"
+#include "kc_internal.cuh"
+
+namespace kc {
+
+constexpr int RS_TILE_THREADS = 256;
+constexpr int RS_TILE_ITEMS = 16;
+constexpr int RS_TILE = RS_TILE_THREADS * RS_TILE_ITEMS;      // 4096 keys per tile
+constexpr int RS_SMALL_THREADS = 512;
+constexpr int RS_SMALL = RS_SMALL_THREADS * RS_TILE_ITEMS;    // 8192 keys, one CTA
+constexpr uint32_t DD_PIECE = 16 * 1024;
+
+static inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+size_t dedup_scratch_bytes(uint64_t P, uint64_t *tiles_out) {
+    const uint64_t tiles = ceil_div(P ? P : 1, RS_TILE);
+    if (tiles_out) *tiles_out = tiles;
+    const uint64_t n = P ? P : 1;
+    size_t b = 0;
+    b += 2 * n * 8;          // keys[2]
+    b += 2 * n * 4;          // vals[2]
+    b += n * 4;              // flags
+    b += n * 8;              // pos
+    b += 64;                 // misc
+    b += 256 * tiles * 4;    // hist
+    b += 256 * tiles * 8;    // hist_off
+    b += 6 * n * 4;          // seg, neq, bad, canon, blob_page, dups
+    b += n * 4;              // reps
+    return b + 16 * 256;     // alignment slack
+}
+
+void dedup_scratch_carve(void *base, uint64_t P, DedupScratch *s) {
+    uint64_t tiles;
+    dedup_scratch_bytes(P, &tiles);
+    const uint64_t n = P ? P : 1;
+    uintptr_t p = reinterpret_cast<uintptr_t>(base);
+    auto take = [&](size_t bytes) {
+        p = (p + 255) & ~(uintptr_t)255;
+        void *r = reinterpret_cast<void *>(p);
+        p += bytes;
+        return r;
+    };
+    s->keys[0] = (uint64_t *)take(n * 8);
+    s->keys[1] = (uint64_t *)take(n * 8);
+    s->vals[0] = (uint32_t *)take(n * 4);
+    s->vals[1] = (uint32_t *)take(n * 4);
+    s->flags = (uint32_t *)take(n * 4);
+    s->pos = (uint64_t *)take(n * 8);
+    s->misc = (uint64_t *)take(64);
+    s->hist = (uint32_t *)take(256 * tiles * 4);
+    s->hist_off = (uint64_t *)take(256 * tiles * 8);
+    s->seg = (uint32_t *)take(n * 4);
+    s->neq = (uint32_t *)take(n * 4);
+    s->bad = (uint32_t *)take(n * 4);
+    s->canon = (uint32_t *)take(n * 4);
+    s->blob_page = (uint32_t *)take(n * 4);
+    s->dups = (uint32_t *)take(n * 4);
+    s->reps = (uint32_t *)take(n * 4);
+    s->capacity_pages = n;
+    s->capacity_tiles = tiles;
+}
+
+// ---- page location ---------------------------------------------------------------
+
+struct PageLoc {
+    const uint8_t *ptr;
+    uint64_t len;
+    uint64_t off;
+    int region;
+};
+
+__device__ __forceinline__ PageLoc locate(const Pages &pg, uint64_t p) {
+    PageLoc l;
+    l.region = region_of(pg.regions, pg.nregions, p);
+    const Region r = pg.regions[l.region];
+    l.off = (p - r.first) << pg.log2page;
+    l.len = r.bytes - l.off < pg.page ? r.bytes - l.off : pg.page;
+    l.ptr = reinterpret_cast<const uint8_t *>(r.base + l.off);
+    return l;
+}
+
+// ---- 1. compaction ----------------------------------------------------------------
+
+__global__ void dd_flag_kernel(const uint8_t *__restrict__ zero, uint64_t P, uint32_t *__restrict__ flags) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x)
+        flags[p] = zero[p] == KC_PAGE_DATA ? 1u : 0u;
+}
+
+__global__ void dd_compact_kernel(const uint64_t *__restrict__ hash, const uint32_t *__restrict__ flags,
+                                  const uint64_t *__restrict__ pos, uint64_t P, uint64_t *__restrict__ keys,
+                                  uint32_t *__restrict__ vals) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x) {
+        if (flags[p]) {
+            keys[pos[p]] = hash[p];
+            vals[pos[p]] = (uint32_t)p;
+        }
+    }
+}
+
+// ---- 2. radix sort ----------------------------------------------------------------
+//
+// Stable ranking inside a group of warps: warp w owns a contiguous run of the
+// input and walks it 32 elements at a time in order; __match_any_sync finds
+// the lanes with the same digit, so an element's rank inside its warp and
+// digit is the warp's running count for that digit plus the number of
+// earlier lanes with that digit.  Warp counts are then scanned digit-major
+// (digit, then warp), which keeps the order of equal digits.
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 0xffu; }
+
+// Rank ITEMS striped elements of this warp; wcnt = this warp's 256 counters.
+template <int ITEMS>
+__device__ __forceinline__ void warp_rank(const uint64_t (&key)[ITEMS], int shift, uint32_t *wcnt,
+                                          uint16_t (&local)[ITEMS]) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+        const uint32_t d = digit_of(key[r], shift);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = __popc(peers & lanemask_lt());
+        const uint32_t base = wcnt[d];
+        local[r] = (uint16_t)(base + before);
+        __syncwarp();
+        if (before == 0) wcnt[d] = base + __popc(peers);
+        __syncwarp();
+    }
+    (void)lane;
+}
+
+// One CTA sorts up to RS_SMALL keys: registers hold the current order, shared
+// memory receives each pass's scatter.
+__global__ void __launch_bounds__(RS_SMALL_THREADS) rs_small_kernel(const uint64_t *__restrict__ keys_in,
+                                                                    const uint32_t *__restrict__ vals_in,
+                                                                    const uint64_t *__restrict__ m_ptr,
+                                                                    uint64_t *__restrict__ keys_out,
+                                                                    uint32_t *__restrict__ vals_out) {
+    constexpr int NW = RS_SMALL_THREADS / 32;
+    constexpr int PER_WARP = 32 * RS_TILE_ITEMS;
+    extern __shared__ __align__(16) uint8_t sm[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(sm);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_SMALL);
+    uint32_t *cnt = sv + RS_SMALL;              // [NW][256]
+    __shared__ uint32_t dsum[256];
+    __shared__ uint32_t dbase[256];
+
+    const uint32_t m = (uint32_t)*m_ptr;
+    if (m == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t key[RS_TILE_ITEMS];
+    uint32_t val[RS_TILE_ITEMS];
+    uint16_t loc[RS_TILE_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_TILE_ITEMS; ++r) {
+        const uint32_t i = warp * PER_WARP + r * 32 + lane;
+        key[r] = i < m ? keys_in[i] : ~0ull;
+        val[r] = i < m ? vals_in[i] : 0xffffffffu;
+    }
+    for (int shift = 0; shift < 64; shift += 8) {
+        for (int i = threadIdx.x; i < NW * 256; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        warp_rank<RS_TILE_ITEMS>(key, shift, cnt + warp * 256, loc);
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t t = cnt[w * 256 + d];
+                cnt[w * 256 + d] = run;
+                run += t;
+            }
+            dsum[d] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            for (int d = 0; d < 256; ++d) {
+                dbase[d] = run;
+                run += dsum[d];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_TILE_ITEMS; ++r) {
+            const uint32_t d = digit_of(key[r], shift);
+            const uint32_t o = dbase[d] + cnt[warp * 256 + d] + loc[r];
+            sk[o] = key[r];
+            sv[o] = val[r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_TILE_ITEMS; ++r) {
+            const uint32_t i = warp * PER_WARP + r * 32 + lane;
+            key[r] = sk[i];
+            val[r] = sv[i];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < RS_TILE_ITEMS; ++r) {
+        const uint32_t i = warp * PER_WARP + r * 32 + lane;
+        if (i < m) {
+            keys_out[i] = key[r];
+            vals_out[i] = val[r];
+        }
+    }
+}
+
+// Tiled pass, part 1: per-tile digit histogram, stored digit-major.
+__global__ void __launch_bounds__(RS_TILE_THREADS) rs_hist_kernel(const uint64_t *__restrict__ keys,
+                                                                  const uint64_t *__restrict__ m_ptr, int shift,
+                                                                  uint32_t *__restrict__ hist, uint32_t ntiles) {
+    __shared__ uint32_t h[256];
+    const uint64_t m = *m_ptr;
+    const uint32_t tile = blockIdx.x;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)tile * RS_TILE;
+    for (int j = threadIdx.x; j < RS_TILE; j += blockDim.x) {
+        const uint64_t i = t0 + j;
+        if (i < m) atomicAdd(&h[digit_of(keys[i], shift)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(uint64_t)d * ntiles + tile] = h[d];
+}
+
+// Tiled pass, part 3: stable scatter of one tile at its scanned offsets.
+__global__ void __launch_bounds__(RS_TILE_THREADS) rs_scatter_kernel(const uint64_t *__restrict__ kin,
+                                                                     const uint32_t *__restrict__ vin,
+                                                                     const uint64_t *__restrict__ m_ptr, int shift,
+                                                                     const uint64_t *__restrict__ hist_off,
+                                                                     uint32_t ntiles, uint64_t *__restrict__ kout,
+                                                                     uint32_t *__restrict__ vout) {
+    constexpr int NW = RS_TILE_THREADS / 32;
+    constexpr int PER_WARP = 32 * RS_TILE_ITEMS;
+    __shared__ uint32_t cnt[NW * 256];
+    __shared__ uint64_t base[256];
+    const uint64_t m = *m_ptr;
+    const uint32_t tile = blockIdx.x;
+    const uint64_t t0 = (uint64_t)tile * RS_TILE;
+    if (t0 >= m) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < NW * 256; i += blockDim.x) cnt[i] = 0;
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) base[d] = hist_off[(uint64_t)d * ntiles + tile];
+    uint64_t key[RS_TILE_ITEMS];
+    uint32_t val[RS_TILE_ITEMS];
+    uint16_t loc[RS_TILE_ITEMS];
+    bool ok[RS_TILE_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_TILE_ITEMS; ++r) {
+        const uint64_t i = t0 + warp * PER_WARP + r * 32 + lane;
+        ok[r] = i < m;
+        key[r] = ok[r] ? kin[i] : ~0ull;   // padding sorts last and is never written
+        val[r] = ok[r] ? vin[i] : 0u;
+    }
+    __syncthreads();
+    warp_rank<RS_TILE_ITEMS>(key, shift, cnt + warp * 256, loc);
+    __syncthreads();
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t t = cnt[w * 256 + d];
+            cnt[w * 256 + d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_TILE_ITEMS; ++r) {
+        if (!ok[r]) continue;
+        const uint32_t d = digit_of(key[r], shift);
+        const uint64_t o = base[d] + cnt[warp * 256 + d] + loc[r];
+        kout[o] = key[r];
+        vout[o] = val[r];
+    }
+}
+
+// ---- 3. segments, neighbours, byte verification ----------------------------------
+//
+// One CTA scans the sorted keys: seg[i] = index of the first element of i's
+// equal-hash run (an inclusive max-scan of "i if head else 0"), and the
+// positions with an equal-hash predecessor are compacted into dups[].
+
+constexpr int SEG_THREADS = 1024;
+
+__global__ void __launch_bounds__(SEG_THREADS) dd_segments_kernel(const uint64_t *__restrict__ keys,
+                                                                  uint64_t *__restrict__ misc,
+                                                                  uint32_t *__restrict__ seg,
+                                                                  uint32_t *__restrict__ dups) {
+    __shared__ uint32_t wmax[32], wsum[32];
+    __shared__ uint32_t carry_max, carry_sum;
+    const uint64_t m = misc[0];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        carry_max = 0;
+        carry_sum = 0;
+    }
+    __syncthreads();
+    for (uint64_t b = 0; b < m; b += SEG_THREADS) {
+        const uint64_t i = b + tid;
+        uint32_t head_idx = 0, dup = 0;
+        if (i < m) {
+            const bool head = (i == 0) || keys[i] != keys[i - 1];
+            head_idx = head ? (uint32_t)i : 0u;
+            dup = head ? 0u : 1u;
+        }
+        uint32_t mx = head_idx, sm = dup;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, mx, o);
+            uint32_t z = __shfl_up_sync(0xffffffffu, sm, o);
+            if (lane >= o) {
+                mx = y > mx ? y : mx;
+                sm += z;
+            }
+        }
+        if (lane == 31) {
+            wmax[warp] = mx;
+            wsum[warp] = sm;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t a = wmax[lane], s = wsum[lane];
+            uint32_t ai = a, si = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, ai, o);
+                uint32_t z = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o) {
+                    ai = y > ai ? y : ai;
+                    si += z;
+                }
+            }
+            // exclusive over warps, combined with the carry of earlier chunks
+            uint32_t ea = __shfl_up_sync(0xffffffffu, ai, 1);
+            uint32_t es = si - s;
+            if (lane == 0) ea = 0;
+            wmax[lane] = ea > carry_max ? ea : carry_max;
+            wsum[lane] = carry_sum + es;
+        }
+        __syncthreads();
+        const uint32_t segv = mx > wmax[warp] ? mx : wmax[warp];
+        const uint32_t dpos = wsum[warp] + sm - dup;
+        if (i < m) {
+            seg[i] = segv;
+            if (dup) dups[dpos] = (uint32_t)i;
+        }
+        __syncthreads();
+        if (tid == SEG_THREADS - 1) {
+            carry_max = segv;
+            carry_sum = dpos + dup;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) misc[2] = carry_sum;
+}
+
+// Byte-compare sorted element i with element i-1, one 16 KiB piece per warp.
+__global__ void __launch_bounds__(256) dd_verify_kernel(Pages pg, const uint32_t *__restrict__ vals,
+                                                        const uint32_t *__restrict__ dups,
+                                                        const uint64_t *__restrict__ misc,
+                                                        uint32_t *__restrict__ neq) {
+    const uint64_t ndup = misc[2];
+    const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
+    const uint64_t items = ndup * pieces;
+    const uint32_t lane = lane_id();
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t it = gw; it < items; it += nw) {
+        const uint32_t i = dups[it / pieces];
+        const uint32_t piece = (uint32_t)(it % pieces);
+        const PageLoc a = locate(pg, vals[i]);
+        const PageLoc b = locate(pg, vals[i - 1]);
+        if (a.len != b.len) {
+            if (lane == 0) neq[i] = 1;
+            continue;
+        }
+        const uint64_t p0 = (uint64_t)piece * DD_PIECE;
+        if (p0 >= a.len) continue;
+        const uint64_t plen = a.len - p0 < DD_PIECE ? a.len - p0 : DD_PIECE;
+        const uint8_t *x = a.ptr + p0, *y = b.ptr + p0;
+        const uint64_t nvec = plen >> 4;
+        bool diff = false;
+        uint64_t v = lane;
+        for (; v + 96 < nvec; v += 128) {
+            uint4 a0 = ldg_stream(x + 16 * v), a1 = ldg_stream(x + 16 * (v + 32));
+            uint4 a2 = ldg_stream(x + 16 * (v + 64)), a3 = ldg_stream(x + 16 * (v + 96));
+            uint4 b0 = ldg_stream(y + 16 * v), b1 = ldg_stream(y + 16 * (v + 32));
+            uint4 b2 = ldg_stream(y + 16 * (v + 64)), b3 = ldg_stream(y + 16 * (v + 96));
+            diff |= (a0.x ^ b0.x) | (a0.y ^ b0.y) | (a0.z ^ b0.z) | (a0.w ^ b0.w);
+            diff |= (a1.x ^ b1.x) | (a1.y ^ b1.y) | (a1.z ^ b1.z) | (a1.w ^ b1.w);
+            diff |= (a2.x ^ b2.x) | (a2.y ^ b2.y) | (a2.z ^ b2.z) | (a2.w ^ b2.w);
+            diff |= (a3.x ^ b3.x) | (a3.y ^ b3.y) | (a3.z ^ b3.z) | (a3.w ^ b3.w);
+        }
+        for (; v < nvec; v += 32) {
+            uint4 a0 = ldg_stream(x + 16 * v), b0 = ldg_stream(y + 16 * v);
+            diff |= (a0.x ^ b0.x) | (a0.y ^ b0.y) | (a0.z ^ b0.z) | (a0.w ^ b0.w);
+        }
+        for (uint64_t t = (nvec << 4) + lane; t < plen; t += 32) diff |= x[t] != y[t];
+        if (__any_sync(0xffffffffu, diff) && lane == 0) neq[i] = 1;
+    }
+}
+
+// ---- 4. classes ------------------------------------------------------------------
+
+// Mark segments holding an element that differs from its predecessor and
+// list each such segment once.
+__global__ void dd_bad_kernel(const uint32_t *__restrict__ dups, const uint32_t *__restrict__ neq,
+                              const uint32_t *__restrict__ seg, uint64_t *__restrict__ misc,
+                              uint32_t *__restrict__ bad, uint32_t *__restrict__ badlist) {
+    const uint64_t ndup = misc[2];
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ndup; j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = dups[j];
+        if (neq[i]) {
+            const uint32_t s = seg[i];
+            if (atomicExch(&bad[s], 1u) == 0u) {
+                const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&misc[3]), 1ull);
+                badlist[slot] = s;
+            }
+        }
+    }
+}
+
+__global__ void dd_canon_kernel(const uint32_t *__restrict__ vals, const uint32_t *__restrict__ seg,
+                                const uint32_t *__restrict__ bad, const uint64_t *__restrict__ misc,
+                                uint32_t *__restrict__ canon) {
+    const uint64_t m = misc[0];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = seg[i];
+        if (!bad[s]) canon[vals[i]] = vals[s];
+    }
+}
+
+__device__ bool cta_pages_equal(const Pages &pg, uint32_t p, uint32_t q) {
+    const PageLoc a = locate(pg, p), b = locate(pg, q);
+    if (a.len != b.len) return false;
+    bool diff = false;
+    const uint64_t nvec = a.len >> 4;
+    for (uint64_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+        const uint4 x = ldg_stream(a.ptr + 16 * v), y = ldg_stream(b.ptr + 16 * v);
+        diff |= (x.x != y.x) | (x.y != y.y) | (x.z != y.z) | (x.w != y.w);
+    }
+    for (uint64_t t = (nvec << 4) + threadIdx.x; t < a.len; t += blockDim.x) diff |= a.ptr[t] != b.ptr[t];
+    return __syncthreads_or(diff) == 0;
+}
+
+// Slow path: one CTA per listed segment assigns classes by direct comparison
+// with the representatives found so far (pages visited in increasing id).
+__global__ void __launch_bounds__(256) dd_slow_kernel(Pages pg, const uint32_t *__restrict__ vals,
+                                                      const uint32_t *__restrict__ seg,
+                                                      const uint32_t *__restrict__ badlist,
+                                                      const uint64_t *__restrict__ misc,
+                                                      uint32_t *__restrict__ reps, uint32_t *__restrict__ canon) {
+    const uint64_t nbad = misc[3];
+    const uint64_t m = misc[0];
+    for (uint64_t b = blockIdx.x; b < nbad; b += gridDim.x) {
+        const uint32_t s = badlist[b];
+        uint32_t nrep = 0;
+        for (uint64_t j = s; j < m && seg[j] == s; ++j) {
+            const uint32_t pj = vals[j];
+            uint32_t found = 0xffffffffu;
+            for (uint32_t r = 0; r < nrep; ++r) {
+                if (cta_pages_equal(pg, pj, reps[s + r])) {
+                    found = reps[s + r];
+                    break;
+                }
+            }
+            if (threadIdx.x == 0) {
+                if (found != 0xffffffffu) canon[pj] = found;
+                else {
+                    reps[s + nrep] = pj;
+                    canon[pj] = pj;
+                }
+            }
+            if (found == 0xffffffffu) ++nrep;
+            __syncthreads();
+        }
+    }
+}
+
+// ---- 5. blobs and the page table ---------------------------------------------------
+
+__global__ void dd_canonflag_kernel(const uint8_t *__restrict__ zero, const uint32_t *__restrict__ canon,
+                                    uint64_t P, uint32_t *__restrict__ flags) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x)
+        flags[p] = (zero[p] == KC_PAGE_DATA && canon[p] == (uint32_t)p) ? 1u : 0u;
+}
+
+__global__ void dd_table_kernel(Pages pg, const uint8_t *__restrict__ zero, const uint32_t *__restrict__ canon,
+                                const uint32_t *__restrict__ flags, const uint64_t *__restrict__ pos,
+                                kc_page *__restrict__ table, uint32_t *__restrict__ blob_page) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < pg.npages;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const int a = region_of(pg.regions, pg.nregions, p);
+        const uint64_t first = pg.regions[a].first;
+        kc_page row;
+        row.va_offset = (p - first) << pg.log2page;
+        row.alloc_id = (uint32_t)a;
+        const uint8_t z = zero[p];
+        if (z == KC_PAGE_ZERO) row.blob = KC_BLOB_ZERO;
+        else if (z == KC_PAGE_LOST) row.blob = KC_BLOB_LOST;
+        else row.blob = (uint32_t)pos[canon[p]];
+        table[p] = row;
+        if (z == KC_PAGE_DATA && flags[p]) blob_page[pos[p]] = (uint32_t)p;
+    }
+}
+
+// ---- 6. pack ----------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) dd_pack_kernel(Pages pg, const uint32_t *__restrict__ blob_page,
+                                                      const uint64_t *__restrict__ misc, uint8_t *__restrict__ arena,
+                                                      uint64_t arena_cap, uint32_t *__restrict__ status) {
+    const uint64_t nb = misc[1];
+    if ((uint64_t)pg.page * nb > arena_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, ST_TRUNC);
+        return;
+    }
+    const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
+    const uint64_t items = nb * pieces;
+    const uint32_t lane = lane_id();
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t it = gw; it < items; it += nw) {
+        const uint64_t b = it / pieces;
+        const uint32_t piece = (uint32_t)(it - b * pieces);
+        const PageLoc l = locate(pg, blob_page[b]);
+        const uint64_t p0 = (uint64_t)piece * DD_PIECE;
+        const uint64_t plen = pg.page - p0 < DD_PIECE ? pg.page - p0 : DD_PIECE;   // slot piece
+        uint8_t *dst = arena + b * pg.page + p0;
+        const uint64_t have = l.len > p0 ? (l.len - p0 < plen ? l.len - p0 : plen) : 0;   // source bytes
+        const uint8_t *src = l.ptr + p0;
+        const uint64_t nvec = have >> 4;
+        uint64_t v = lane;
+        for (; v + 96 < nvec; v += 128) {
+            uint4 x0 = ldg_stream(src + 16 * v), x1 = ldg_stream(src + 16 * (v + 32));
+            uint4 x2 = ldg_stream(src + 16 * (v + 64)), x3 = ldg_stream(src + 16 * (v + 96));
+            *reinterpret_cast<uint4 *>(dst + 16 * v) = x0;
+            *reinterpret_cast<uint4 *>(dst + 16 * (v + 32)) = x1;
+            *reinterpret_cast<uint4 *>(dst + 16 * (v + 64)) = x2;
+            *reinterpret_cast<uint4 *>(dst + 16 * (v + 96)) = x3;
+        }
+        for (; v < nvec; v += 32) *reinterpret_cast<uint4 *>(dst + 16 * v) = ldg_stream(src + 16 * v);
+        // bytes [16*nvec, have) copied one by one, [have, plen) zero-filled
+        const uint64_t z0 = (have + 15) & ~15ull;
+        for (uint64_t t = (nvec << 4) + lane; t < z0 && t < plen; t += 32) dst[t] = t < have ? src[t] : 0;
+        const uint4 zz = make_uint4(0, 0, 0, 0);
+        for (uint64_t t = z0 + 16 * lane; t + 16 <= plen; t += 512) *reinterpret_cast<uint4 *>(dst + t) = zz;
+    }
+}
+
+// ---- driver ------------------------------------------------------------------------
+
+static inline unsigned grid_for(uint64_t n, int threads, int sms, int per_sm) {
+    uint64_t b = (n + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)sms * per_sm;
+    if (b > cap) b = cap;
+    return (unsigned)(b ? b : 1);
+}
+
+#define KC_TRY(x)                                   \
+    do {                                            \
+        cudaError_t e_ = (x);                       \
+        if (e_ != cudaSuccess) return e_;           \
+    } while (0)
+
+cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero, kc_page *table,
+                      uint8_t *arena, uint64_t arena_cap, uint64_t *n_blobs, DedupScratch &s,
+                      uint32_t *status, int sms, cudaStream_t st) {
+    const uint64_t P = pg.npages;
+    const unsigned g = grid_for(P, 256, sms, 8);
+    KC_TRY(cudaMemsetAsync(s.misc, 0, 64, st));
+    KC_TRY(cudaMemsetAsync(s.neq, 0, P * 4, st));
+    KC_TRY(cudaMemsetAsync(s.bad, 0, P * 4, st));
+    // 1. compaction
+    dd_flag_kernel<<<g, 256, 0, st>>>(zero, P, s.flags);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    KC_TRY(launch_scan_u32(s.flags, s.pos, P, &s.misc[0], st));
+    dd_compact_kernel<<<g, 256, 0, st>>>(hash, s.flags, s.pos, P, s.keys[0], s.vals[0]);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    // 2. sort (m <= P)
+    if (P <= (uint64_t)RS_SMALL) {
+        const size_t smem = (size_t)RS_SMALL * 12 + (RS_SMALL_THREADS / 32) * 256 * 4;
+        KC_TRY(cudaFuncSetAttribute(rs_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        rs_small_kernel<<<1, RS_SMALL_THREADS, smem, st>>>(s.keys[0], s.vals[0], &s.misc[0], s.keys[0], s.vals[0]);
+        count_launches(1);
+        KC_TRY(cudaGetLastError());
+    } else {
+        const uint32_t ntiles = (uint32_t)ceil_div(P, RS_TILE);
+        int src = 0;
+        for (int shift = 0; shift < 64; shift += 8) {
+            rs_hist_kernel<<<ntiles, RS_TILE_THREADS, 0, st>>>(s.keys[src], &s.misc[0], shift, s.hist, ntiles);
+            count_launches(1);
+            KC_TRY(cudaGetLastError());
+            KC_TRY(launch_scan_u32(s.hist, s.hist_off, 256ull * ntiles, nullptr, st));
+            rs_scatter_kernel<<<ntiles, RS_TILE_THREADS, 0, st>>>(s.keys[src], s.vals[src], &s.misc[0], shift,
+                                                                  s.hist_off, ntiles, s.keys[src ^ 1],
+                                                                  s.vals[src ^ 1]);
+            count_launches(1);
+            KC_TRY(cudaGetLastError());
+            src ^= 1;
+        }
+        // eight passes: the result is back in buffer 0
+    }
+    // 3. segments, neighbours, verification
+    dd_segments_kernel<<<1, SEG_THREADS, 0, st>>>(s.keys[0], s.misc, s.seg, s.dups);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
+    dd_verify_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.vals[0], s.dups, s.misc, s.neq);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    // 4. classes
+    dd_bad_kernel<<<g, 256, 0, st>>>(s.dups, s.neq, s.seg, s.misc, s.bad, s.flags);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    dd_canon_kernel<<<g, 256, 0, st>>>(s.vals[0], s.seg, s.bad, s.misc, s.canon);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    dd_slow_kernel<<<(unsigned)sms, 256, 0, st>>>(pg, s.vals[0], s.seg, s.flags, s.misc, s.reps, s.canon);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    // 5. blobs and table
+    dd_canonflag_kernel<<<g, 256, 0, st>>>(zero, s.canon, P, s.flags);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    KC_TRY(launch_scan_u32(s.flags, s.pos, P, &s.misc[1], st));
+    dd_table_kernel<<<g, 256, 0, st>>>(pg, zero, s.canon, s.flags, s.pos, table, s.blob_page);
+    count_launches(1);
+    KC_TRY(cudaGetLastError());
+    if (n_blobs) KC_TRY(cudaMemcpyAsync(n_blobs, &s.misc[1], 8, cudaMemcpyDeviceToDevice, st));
+    // 6. pack
+    if (arena) {
+        dd_pack_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.blob_page, s.misc, arena,
+                                                                               arena_cap, status);
+        count_launches(1);
+        KC_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+}  // namespace kc

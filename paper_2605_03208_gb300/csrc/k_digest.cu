@@ -1,0 +1,495 @@
+// k_digest.cu -- page digest (XXH64 seed 0 + zero flag), optionally fused
+// with the pointer-census count, and the census count / write / scan kernels.
+//
+// Digest mapping.  XXH64 keeps four serial accumulators, one per 8-byte lane
+// of every 32-byte stripe, so one page is hashed by a quad of four threads
+// (thread k owns accumulator k).  A warp hashes eight pages at once (one per
+// quad) and takes its next eight pages from a global ticket counter, so
+// warps that finish early steal the remaining work.  Each warp owns a ring of
+// `stages` shared-memory stages; a stage holds one `chunk` of each of its
+// eight pages, fetched by one bulk copy (cp.async.bulk, the TMA's 1-D form)
+// per page that completes on the stage's mbarrier.  The first thread of each
+// quad issues its page's copy, so a stage barrier expects eight arrivals.
+// Page slots are padded by 32 bytes so the eight quads' 8-byte shared loads
+// spread over all 32 banks.  The < 32-byte tail of a page (and the < 16-byte
+// part a bulk copy cannot move) is read from global memory by the quad
+// leader while it finishes the hash.
+#include <cuda_runtime.h>
+
+#include "kc_device.cuh"
+#include "kc_internal.cuh"
+
+namespace kc {
+
+static __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+size_t digest_smem_bytes(const DigestShape &s) {
+    size_t bars = align_up((size_t)s.warps * s.stages * sizeof(uint64_t), 128);
+    size_t ring = (size_t)s.warps * s.stages * 8 * (size_t)(s.chunk + 32);
+    return bars + ring;
+}
+
+template <bool CENSUS>
+__global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, uint64_t *__restrict__ hash,
+                                                     uint8_t *__restrict__ zero,
+                                                     uint32_t *__restrict__ page_hits,
+                                                     uint64_t *__restrict__ counts,
+                                                     uint32_t *__restrict__ task_ctr,
+                                                     uint32_t *__restrict__ status, int stages,
+                                                     int chunk) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const int q = lane >> 2;   // page slot of this quad
+    const int k = lane & 3;    // XXH64 accumulator owned by this thread
+    const uint32_t FULL = 0xffffffffu;
+
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem) + warp * stages;
+    const size_t slot_stride = (size_t)chunk + 32;
+    const size_t stage_stride = 8 * slot_stride;
+    uint8_t *ring = smem + align_up((size_t)nwarps * stages * sizeof(uint64_t), 128) +
+                    (size_t)warp * stages * stage_stride;
+
+    if (lane < (uint32_t)stages) mbar_init(&bars[lane], 8);
+    mbar_fence_init();
+    __syncwarp();
+
+    uint64_t pos = 0;   // ring positions consumed by this warp so far
+    while (true) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(task_ctr, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        const uint64_t p0 = (uint64_t)t * 8;
+        if (p0 >= pg.npages) break;
+        const uint64_t p = p0 + q;
+        const bool valid = p < pg.npages;
+
+        const uint8_t *src = nullptr;
+        uint64_t len = 0, off = 0;
+        uint32_t region = 0;
+        bool lost = false;
+        if (valid) {
+            region = (uint32_t)region_of(pg.regions, pg.nregions, p);
+            const Region r = pg.regions[region];
+            off = (p - r.first) << pg.log2page;
+            len = r.bytes - off < pg.page ? r.bytes - off : pg.page;
+            src = reinterpret_cast<const uint8_t *>(r.base + off);
+            lost = r.lost != 0;
+        }
+        const uint32_t sbytes = lost ? 0u : (uint32_t)(len & ~31ull);   // bytes in full stripes
+        const uint32_t nch = (sbytes + chunk - 1) / chunk;
+        const uint32_t maxch = __reduce_max_sync(FULL, nch);
+
+        // Issue chunk c of this task into ring position pos + c.
+        auto issue = [&](uint32_t c) {
+            const uint64_t g = pos + c;
+            const int st = (int)(g % stages);
+            if (k == 0) {
+                uint32_t b = 0;
+                if (c < nch) {
+                    const uint32_t rest = sbytes - c * chunk;
+                    b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
+                }
+                uint64_t *bar = &bars[st];
+                if (b) {
+                    mbar_arrive_expect_tx(bar, b);
+                    bulk_g2s(ring + st * stage_stride + q * slot_stride, src + (size_t)c * chunk, b, bar);
+                } else {
+                    mbar_arrive(bar);
+                }
+            }
+        };
+        const uint32_t pre = maxch < (uint32_t)stages ? maxch : (uint32_t)stages;
+        for (uint32_t c = 0; c < pre; ++c) issue(c);
+
+        uint64_t acc = xx_init(k);
+        uint64_t zor = 0;
+        uint32_t hin = 0, hout = 0;
+        bool timed_out = false;
+        uint32_t c = 0;
+        for (; c < maxch; ++c) {
+            const uint64_t g = pos + c;
+            const int st = (int)(g % stages);
+            const uint32_t parity = (uint32_t)((g / stages) & 1);
+            const bool ok = mbar_wait_bounded(&bars[st], parity);
+            if (!__all_sync(FULL, ok)) {
+                timed_out = true;
+                break;
+            }
+            uint32_t b = 0;
+            if (c < nch) {
+                const uint32_t rest = sbytes - c * chunk;
+                b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
+            }
+            const uint8_t *slot = ring + st * stage_stride + q * slot_stride + 8 * k;
+            uint32_t s = 0;
+            for (; s + 128 <= b; s += 128) {
+                uint64_t w0 = *reinterpret_cast<const uint64_t *>(slot + s);
+                uint64_t w1 = *reinterpret_cast<const uint64_t *>(slot + s + 32);
+                uint64_t w2 = *reinterpret_cast<const uint64_t *>(slot + s + 64);
+                uint64_t w3 = *reinterpret_cast<const uint64_t *>(slot + s + 96);
+                acc = xx_round(acc, w0);
+                acc = xx_round(acc, w1);
+                acc = xx_round(acc, w2);
+                acc = xx_round(acc, w3);
+                zor |= (w0 | w1) | (w2 | w3);
+                if (CENSUS) {
+                    int32_t tg;
+                    uint64_t ws[4] = {w0, w1, w2, w3};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        int cl = census_classify(ca, ws[u], &tg);
+                        hin += cl == 1;
+                        hout += cl == 2;
+                    }
+                }
+            }
+            for (; s < b; s += 32) {
+                uint64_t w = *reinterpret_cast<const uint64_t *>(slot + s);
+                acc = xx_round(acc, w);
+                zor |= w;
+                if (CENSUS) {
+                    int32_t tg;
+                    int cl = census_classify(ca, w, &tg);
+                    hin += cl == 1;
+                    hout += cl == 2;
+                }
+            }
+            __syncwarp();
+            if (c + stages < maxch) issue(c + stages);
+        }
+        if (timed_out) {
+            // Give the copies still in flight a bounded chance to land before
+            // this warp stops using its ring, then report and quit.
+            const uint32_t issued = (c + stages < maxch) ? c + stages : maxch;
+            for (uint32_t c2 = c; c2 < issued; ++c2) {
+                const uint64_t g = pos + c2;
+                mbar_wait_bounded(&bars[g % stages], (uint32_t)((g / stages) & 1));
+            }
+            if (lane == 0) set_status(status, ST_TIMEOUT);
+            break;
+        }
+        pos += maxch;
+
+        // Quad reduction: accumulators to the quad leader, OR of bytes, hit counts.
+        const int qb = lane & ~3;
+        const uint64_t a1 = __shfl_sync(FULL, acc, qb + 1);
+        const uint64_t a2 = __shfl_sync(FULL, acc, qb + 2);
+        const uint64_t a3 = __shfl_sync(FULL, acc, qb + 3);
+        zor |= __shfl_xor_sync(FULL, zor, 1);
+        zor |= __shfl_xor_sync(FULL, zor, 2);
+        if (CENSUS) {
+            hin += __shfl_xor_sync(FULL, hin, 1);
+            hin += __shfl_xor_sync(FULL, hin, 2);
+            hout += __shfl_xor_sync(FULL, hout, 1);
+            hout += __shfl_xor_sync(FULL, hout, 2);
+        }
+        if (k == 0 && valid) {
+            if (lost) {
+                hash[p] = 0;
+                zero[p] = KC_PAGE_LOST;
+                if (CENSUS) page_hits[p] = 0;
+            } else {
+                uint64_t h;
+                if (len >= 32) {
+                    h = rotl(acc, 1) + rotl(a1, 7) + rotl(a2, 12) + rotl(a3, 18);
+                    h = (h ^ xx_round(0, acc)) * XXP1 + XXP4;
+                    h = (h ^ xx_round(0, a1)) * XXP1 + XXP4;
+                    h = (h ^ xx_round(0, a2)) * XXP1 + XXP4;
+                    h = (h ^ xx_round(0, a3)) * XXP1 + XXP4;
+                } else {
+                    h = XXP5;
+                }
+                h += len;
+                const uint8_t *tp = src + sbytes;
+                uint32_t rem = (uint32_t)(len - sbytes);
+                uint64_t toff = off + sbytes;
+                while (rem >= 8) {
+                    const uint64_t w = ldg_u64(tp);
+                    h ^= xx_round(0, w);
+                    h = rotl(h, 27) * XXP1 + XXP4;
+                    zor |= w;
+                    if (CENSUS) {
+                        int32_t tg;
+                        int cl = census_classify(ca, w, &tg);
+                        hin += cl == 1;
+                        hout += cl == 2;
+                    }
+                    tp += 8;
+                    toff += 8;
+                    rem -= 8;
+                }
+                if (rem >= 4) {
+                    const uint32_t w = __ldg(reinterpret_cast<const unsigned int *>(tp));
+                    h ^= (uint64_t)w * XXP1;
+                    h = rotl(h, 23) * XXP2 + XXP3;
+                    zor |= w;
+                    tp += 4;
+                    rem -= 4;
+                }
+                while (rem) {
+                    const uint32_t bb = __ldg(tp);
+                    h ^= (uint64_t)bb * XXP5;
+                    h = rotl(h, 11) * XXP1;
+                    zor |= bb;
+                    ++tp;
+                    --rem;
+                }
+                h ^= h >> 33;
+                h *= XXP2;
+                h ^= h >> 29;
+                h *= XXP3;
+                h ^= h >> 32;
+                hash[p] = h;
+                zero[p] = zor == 0 ? KC_PAGE_ZERO : KC_PAGE_DATA;
+                if (CENSUS) {
+                    page_hits[p] = hin + hout;
+                    if (hin) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), hin);
+                    if (hout) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), hout);
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash, uint8_t *zero,
+                          uint32_t *page_hits, uint64_t *counts, uint32_t *task_ctr, uint32_t *status,
+                          const DigestShape &shape, cudaStream_t st) {
+    const size_t smem = digest_smem_bytes(shape);
+    const dim3 block(32 * shape.warps), grid(shape.ctas);
+    cudaError_t e;
+    if (census) {
+        e = cudaFuncSetAttribute(digest_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        digest_kernel<true><<<grid, block, smem, st>>>(pg, *census, hash, zero, page_hits, counts,
+                                                       task_ctr, status, shape.stages, shape.chunk);
+        count_launches(1);
+    } else {
+        e = cudaFuncSetAttribute(digest_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        CensusArgs none{};
+        digest_kernel<false><<<grid, block, smem, st>>>(pg, none, hash, zero, nullptr, nullptr,
+                                                        task_ctr, status, shape.stages, shape.chunk);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// ---- census: count pass ---------------------------------------------------------
+//
+// Units are fixed-size chunks of the regions (the page size for the fused
+// path, 64 KiB for the standalone call).  One CTA counts one unit with
+// 16-byte streaming loads and writes the unit's hit count; nothing else is
+// written, so the scan over units can place every unit's hits in order.
+
+constexpr int CENSUS_THREADS = 256;
+
+__device__ __forceinline__ void census_word(const CensusArgs &ca, uint64_t v, uint32_t &hin,
+                                            uint32_t &hout) {
+    int32_t tg;
+    int cl = census_classify(ca, v, &tg);
+    hin += cl == 1;
+    hout += cl == 2;
+}
+
+__global__ void __launch_bounds__(CENSUS_THREADS) census_count_kernel(Pages u, CensusArgs ca,
+                                                                      uint32_t *__restrict__ unit_hits,
+                                                                      uint64_t *__restrict__ counts) {
+    __shared__ uint32_t red_in[CENSUS_THREADS / 32], red_out[CENSUS_THREADS / 32];
+    for (uint64_t unit = blockIdx.x; unit < u.npages; unit += gridDim.x) {
+        const int a = region_of(u.regions, u.nregions, unit);
+        const Region r = u.regions[a];
+        uint32_t hin = 0, hout = 0;
+        if (!r.lost) {
+            const uint64_t off = (unit - r.first) << u.log2page;
+            const uint64_t len = r.bytes - off < u.page ? r.bytes - off : u.page;
+            const uint8_t *base = reinterpret_cast<const uint8_t *>(r.base + off);
+            const uint64_t nwords = len >> 3;
+            const uint64_t nvec = nwords >> 1;
+            uint64_t i = threadIdx.x;
+            for (; i + 3 * CENSUS_THREADS < nvec; i += 4 * CENSUS_THREADS) {
+                uint4 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] = ldg_stream(base + 16 * (i + j * CENSUS_THREADS));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    census_word(ca, ((uint64_t)v[j].y << 32) | v[j].x, hin, hout);
+                    census_word(ca, ((uint64_t)v[j].w << 32) | v[j].z, hin, hout);
+                }
+            }
+            for (; i < nvec; i += CENSUS_THREADS) {
+                uint4 v = ldg_stream(base + 16 * i);
+                census_word(ca, ((uint64_t)v.y << 32) | v.x, hin, hout);
+                census_word(ca, ((uint64_t)v.w << 32) | v.z, hin, hout);
+            }
+            if ((nwords & 1) && threadIdx.x == 0) census_word(ca, ldg_u64(base + 8 * (nwords - 1)), hin, hout);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            hin += __shfl_xor_sync(0xffffffffu, hin, o);
+            hout += __shfl_xor_sync(0xffffffffu, hout, o);
+        }
+        if (lane_id() == 0) {
+            red_in[threadIdx.x >> 5] = hin;
+            red_out[threadIdx.x >> 5] = hout;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t si = 0, so = 0;
+            for (int w = 0; w < CENSUS_THREADS / 32; ++w) {
+                si += red_in[w];
+                so += red_out[w];
+            }
+            unit_hits[unit] = si + so;
+            if (si) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), si);
+            if (so) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), so);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
+                                uint64_t *counts, int sms, cudaStream_t st) {
+    uint64_t blocks = units.npages;
+    const uint64_t maxb = (uint64_t)sms * 8;
+    if (blocks > maxb) blocks = maxb;
+    if (blocks == 0) return cudaSuccess;
+    census_count_kernel<<<(unsigned)blocks, CENSUS_THREADS, 0, st>>>(units, ca, unit_hits, counts);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---- census: ordered write pass ---------------------------------------------------
+//
+// One warp per unit that holds hits: it walks the unit's words in order,
+// 32 at a time, and places each hit at unit_off[unit] + (hits before it in
+// the unit), using a ballot for the in-warp rank.  Only units with hits are
+// read again.
+
+__global__ void __launch_bounds__(256) census_write_kernel(Pages u, CensusArgs ca,
+                                                           const uint32_t *__restrict__ unit_hits,
+                                                           const uint64_t *__restrict__ unit_off,
+                                                           kc_hit *__restrict__ hits, uint64_t cap,
+                                                           uint32_t *__restrict__ status) {
+    const uint32_t lane = lane_id();
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw_total = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t unit = gw; unit < u.npages; unit += nw_total) {
+        const uint32_t cnt = unit_hits[unit];
+        if (cnt == 0) continue;
+        const int a = region_of(u.regions, u.nregions, unit);
+        const Region r = u.regions[a];
+        const uint64_t off = (unit - r.first) << u.log2page;
+        const uint64_t len = r.bytes - off < u.page ? r.bytes - off : u.page;
+        const uint8_t *base = reinterpret_cast<const uint8_t *>(r.base + off);
+        const uint64_t nwords = len >> 3;
+        const uint64_t out = unit_off[unit];
+        uint32_t written = 0;
+        for (uint64_t w0 = 0; w0 < nwords; w0 += 32) {
+            const uint64_t w = w0 + lane;
+            int cl = 0;
+            int32_t tg = -1;
+            uint64_t v = 0;
+            if (w < nwords) {
+                v = ldg_u64(base + 8 * w);
+                cl = census_classify(ca, v, &tg);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, cl != 0);
+            if (cl) {
+                const uint64_t idx = out + written + __popc(bal & lanemask_lt());
+                if (idx < cap) {
+                    kc_hit h;
+                    h.src_offset = off + 8 * w;
+                    h.value = v;
+                    h.src_alloc = (uint32_t)a;
+                    h.target = tg;
+                    hits[idx] = h;
+                }
+            }
+            written += __popc(bal);
+        }
+        if (lane == 0) {
+            if (written != cnt) set_status(status, ST_INTERNAL);
+            if (out + cnt > cap) set_status(status, ST_TRUNC);
+        }
+    }
+}
+
+cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca, const uint32_t *unit_hits,
+                                const uint64_t *unit_off, kc_hit *hits, uint64_t cap, uint32_t *status,
+                                int sms, cudaStream_t st) {
+    uint64_t warps = units.npages;
+    uint64_t blocks = (warps + 7) / 8;
+    uint64_t maxb = (uint64_t)sms * 8;
+    if (blocks > maxb) blocks = maxb;
+    if (blocks == 0) return cudaSuccess;
+    census_write_kernel<<<(unsigned)blocks, 256, 0, st>>>(units, ca, unit_hits, unit_off, hits, cap, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---- single-CTA exclusive scan ------------------------------------------------
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 8;
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_u32_kernel(const uint32_t *__restrict__ in,
+                                                                uint64_t *__restrict__ out, uint64_t n,
+                                                                uint64_t *__restrict__ total) {
+    __shared__ uint64_t warp_sum[SCAN_THREADS / 32];
+    __shared__ uint64_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (uint64_t base = 0; base < n; base += (uint64_t)SCAN_THREADS * SCAN_ITEMS) {
+        uint32_t v[SCAN_ITEMS];
+        uint64_t local = 0;
+        const uint64_t i0 = base + (uint64_t)tid * SCAN_ITEMS;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            v[j] = (i0 + j < n) ? in[i0 + j] : 0u;
+            local += v[j];
+        }
+        uint64_t incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t ws = warp_sum[lane];
+            uint64_t wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            warp_sum[lane] = wi - ws;   // exclusive prefix of warps
+        }
+        __syncthreads();
+        uint64_t run = carry_s + warp_sum[warp] + (incl - local);
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            if (i0 + j < n) out[i0 + j] = run;
+            run += v[j];
+        }
+        __syncthreads();
+        if (tid == SCAN_THREADS - 1) carry_s = run;
+        __syncthreads();
+    }
+    if (tid == 0 && total) *total = carry_s;
+}
+
+cudaError_t launch_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t *total,
+                            cudaStream_t st) {
+    scan_u32_kernel<<<1, SCAN_THREADS, 0, st>>>(in, out, n, total);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace kc

@@ -1,0 +1,168 @@
+// kc_device.cuh -- device helpers: inline PTX for mbarriers and bulk
+// (TMA, non-tensor) copies, bounded waits, warp utilities, XXH64 pieces.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+
+// Polls of an mbarrier before a wait is declared timed out: the first
+// SPIN_FAST polls spin, the rest back off with nanosleep, bounding a wait to
+// roughly a second.
+constexpr uint32_t SPIN_FAST = 256;
+constexpr uint32_t SPIN_LIMIT = 1u << 24;
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier ---------------------------------------------------------------
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make mbarrier initialisation visible to the async proxy (bulk copies).
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t tx) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(tx)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` to complete, at most SPIN_LIMIT polls.
+// Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < SPIN_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= SPIN_FAST) __nanosleep(64);
+    }
+    return false;
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits) {
+    if (status) atomicOr(status, bits);
+}
+
+// ---- loads ------------------------------------------------------------------
+
+__device__ __forceinline__ uint4 ldg_stream(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ldg_u64(const void *p) {
+    return __ldg(reinterpret_cast<const unsigned long long *>(p));
+}
+
+// ---- region lookup ----------------------------------------------------------
+
+// Region holding flattened unit `u`: the last region whose first unit <= u.
+__device__ __forceinline__ int region_of(const Region *r, int n, uint64_t u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(reinterpret_cast<const unsigned long long *>(&r[mid].first)) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- census classification ---------------------------------------------------
+
+// Classify word v: 0 = not a hit, 1 = inside (target in *tgt), 2 = outside.
+__device__ __forceinline__ int census_classify(const CensusArgs &ca, uint64_t v, int32_t *tgt) {
+    bool in_span = (v - ca.span_lo) < ca.span_len;
+    bool in_win = (v - ca.win_lo) < ca.win_len;
+    if (!(in_span || in_win)) return 0;
+    if (in_span) {
+        // first range with base > v, then check the one before it
+        int lo = 0, hi = ca.nranges;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (ldg_u64(&ca.ranges[mid].base) <= v) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo > 0 && v < ldg_u64(&ca.ranges[lo - 1].end)) {
+            *tgt = __ldg(&ca.ranges[lo - 1].id);
+            return 1;
+        }
+    }
+    if (in_win) {
+        *tgt = -1;
+        return 2;
+    }
+    return 0;
+}
+
+// ---- XXH64 (public xxHash specification) -------------------------------------
+
+constexpr uint64_t XXP1 = 0x9E3779B185EBCA87ULL;
+constexpr uint64_t XXP2 = 0xC2B2AE3D27D4EB4FULL;
+constexpr uint64_t XXP3 = 0x165667B19E3779F9ULL;
+constexpr uint64_t XXP4 = 0x85EBCA77C2B2AE63ULL;
+constexpr uint64_t XXP5 = 0x27D4EB2F165667C5ULL;
+
+__device__ __forceinline__ uint64_t rotl(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+// Accumulator step for one 8-byte lane of a stripe.
+__device__ __forceinline__ uint64_t xx_round(uint64_t acc, uint64_t lane) {
+    return rotl(acc + lane * XXP2, 31) * XXP1;
+}
+
+// Seed-0 start value of accumulator k (0..3).
+__device__ __forceinline__ uint64_t xx_init(int k) {
+    return k == 0 ? XXP1 + XXP2 : k == 1 ? XXP2 : k == 2 ? 0ULL : 0ULL - XXP1;
+}
+
+}  // namespace kc

@@ -1,0 +1,133 @@
+// kc_internal.cuh -- types and launch entry points shared by the library's
+// translation units (host planner in kc_api.cu, kernels in k_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kc.h"
+
+namespace kc {
+
+// Device-side condition bits, OR-ed into the context's status word.
+enum : uint32_t {
+    ST_TRUNC = 1u << 0,    // an output capacity was exceeded
+    ST_TIMEOUT = 1u << 1,  // a bounded wait gave up
+    ST_BADROW = 1u << 2,   // a page-table row pointed outside a region/arena
+    ST_INTERNAL = 1u << 3  // an internal consistency check failed
+};
+
+// One region as the kernels see it (32 bytes).  `first` is the id of the
+// region's first unit (page or census chunk) in the flattened unit space.
+struct Region {
+    uint64_t base;
+    uint64_t bytes;
+    uint64_t first;
+    uint32_t lost;   // 1: region not readable, skip it
+    uint32_t pad;
+};
+
+// Census range, sorted by base (24 bytes).
+struct Range {
+    uint64_t base;
+    uint64_t end;
+    int32_t id;
+    int32_t pad;
+};
+
+// Census parameters: a word v is a candidate iff it lies in the captured
+// span [span_lo, span_lo + span_len) or the window [win_lo, win_lo + win_len).
+struct CensusArgs {
+    const Range *ranges;
+    int nranges;
+    uint64_t span_lo, span_len;
+    uint64_t win_lo, win_len;
+};
+
+// Work description shared by the page-granular kernels.
+struct Pages {
+    const Region *regions;
+    int nregions;
+    uint64_t npages;   // P
+    uint32_t page;     // bytes per page (power of two)
+    uint32_t log2page;
+};
+
+// Digest kernel shape (chosen by the host planner or the autotuner).
+struct DigestShape {
+    int warps;        // warps per CTA
+    int stages;       // ring depth per warp
+    int chunk;        // bytes per page per stage (multiple of 32, <= page)
+    int ctas;         // grid size
+};
+
+size_t digest_smem_bytes(const DigestShape &s);
+
+// Process-wide count of kernels launched by this library (every launcher
+// adds its launches); read by kc_launch_count().
+void count_launches(uint64_t n);
+uint64_t launches_so_far();
+
+// Launchers (each returns the cudaError_t of its launch).
+// `census` NULL: digest only.  Otherwise page_hits[P] and counts[2]
+// ({inside, outside}, zeroed by the caller) receive the census counts.
+cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash,
+                          uint8_t *zero, uint32_t *page_hits, uint64_t *counts,
+                          uint32_t *task_ctr, uint32_t *status, const DigestShape &shape,
+                          cudaStream_t st);
+cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
+                                uint64_t *counts, int sms, cudaStream_t st);
+cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca,
+                                const uint32_t *unit_hits, const uint64_t *unit_off,
+                                kc_hit *hits, uint64_t cap, uint32_t *status, int sms,
+                                cudaStream_t st);
+
+// Single-CTA exclusive scan of n u32 values into u64 offsets; total -> *total.
+cudaError_t launch_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t *total,
+                            cudaStream_t st);
+
+// Dedup pipeline (k_dedup.cu).
+struct DedupScratch {
+    uint64_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t *flags;      // per page
+    uint64_t *pos;        // per page scan output
+    uint64_t *misc;       // small counters: [0] m (non-zero pages), [1] n_blobs, [2] ndup
+    uint32_t *hist;       // radix histograms (256 * ntiles)
+    uint64_t *hist_off;   // scanned histograms
+    uint32_t *seg;        // per sorted element: segment start index
+    uint32_t *neq;        // per sorted element: 1 if bytes differ from predecessor
+    uint32_t *bad;        // per sorted element: segment needs the slow path
+    uint32_t *canon;      // per page: canonical page id
+    uint32_t *blob_page;  // per blob: canonical page id
+    uint32_t *dups;       // compacted positions with an equal-hash predecessor
+    uint32_t *reps;       // slow path representatives
+    uint64_t capacity_pages;
+    uint64_t capacity_tiles;
+};
+size_t dedup_scratch_bytes(uint64_t P, uint64_t *tiles_out);
+void dedup_scratch_carve(void *base, uint64_t P, DedupScratch *s);
+cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero, kc_page *table,
+                      uint8_t *arena, uint64_t arena_cap, uint64_t *n_blobs, DedupScratch &s,
+                      uint32_t *status, int sms, cudaStream_t st);
+
+// Restore (k_restore.cu).
+cudaError_t launch_restore(const Pages &pg, const kc_page *table, uint64_t nrows,
+                           const uint8_t *arena, uint64_t arena_bytes, uint32_t *status, int sms,
+                           cudaStream_t st);
+
+// Compare (k_compare.cu).
+struct CmpPair {
+    uint64_t got;
+    uint64_t want;
+    uint64_t nelem;
+    uint64_t tile_first;   // first global tile id of this pair
+    int32_t dtype;
+    int32_t lost;
+};
+cudaError_t launch_compare(const CmpPair *pairs, int npairs, uint64_t ntiles, double atol,
+                           double rtol, kc_cmp_result *out, const int32_t *init_status,
+                           int sms, cudaStream_t st);
+constexpr uint32_t CMP_TILE_BYTES = 64 * 1024;
+
+}  // namespace kc

@@ -1,0 +1,246 @@
+"""Python binding of the C ABI in ``include/kc.h`` (argument marshalling only).
+
+Every operation runs in the CUDA kernels of ``libkc.so``; this module only
+turns torch tensors / integers into the pointers and sizes the C functions
+take.  There is no CPU fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, EOVERLAP, ENOMEM, ETRUNC, ECUDA, ETIMEOUT, EBUF = range(8)
+U8, I32, F16, BF16, F32, RAW = range(6)
+BUF_LOST = 0x1
+PAGE_DATA, PAGE_ZERO, PAGE_LOST = 0, 1, 2
+BLOB_ZERO = 0xFFFFFFFF
+BLOB_LOST = 0xFFFFFFFE
+
+PAGE_DTYPE = np.dtype([("va_offset", "<u8"), ("alloc_id", "<u4"), ("blob", "<u4")])
+HIT_DTYPE = np.dtype([("src_offset", "<u8"), ("value", "<u8"), ("src_alloc", "<u4"),
+                      ("target", "<i4")])
+CMP_DTYPE = np.dtype([("mismatches", "<u8"), ("first", "<i8"), ("max_abs", "<f8"),
+                      ("max_rel", "<f8"), ("nan_got", "<u8"), ("nan_want", "<u8"),
+                      ("nan_mismatch", "<u8"), ("status", "<i4"), ("reserved", "<u4")])
+ESIZE = {U8: 1, RAW: 1, I32: 4, F16: 2, BF16: 2, F32: 4}
+
+# Names declared in include/kc.h (the ABI surface).
+EXPORTS = ["kc_version", "kc_launch_count", "kc_status_name", "kc_last_error", "kc_create", "kc_destroy", "kc_sync",
+           "kc_buf_status", "kc_set_digest_shape", "kc_set_trace_events", "kc_get_digest_shape", "kc_page_count",
+           "kc_digest", "kc_census", "kc_scan", "kc_dedup", "kc_restore", "kc_compare"]
+
+
+class KcBuf(ctypes.Structure):
+    _fields_ = [("base_va", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
+                ("dtype", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class KcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libkc.so (optionally building it first).  Raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    st = ctypes.c_int
+    L.kc_version.restype = i32
+    L.kc_launch_count.restype = u64
+    L.kc_status_name.restype = ctypes.c_char_p
+    L.kc_status_name.argtypes = [i32]
+    L.kc_last_error.restype = ctypes.c_char_p
+    L.kc_last_error.argtypes = [vp]
+    L.kc_create.restype = st
+    L.kc_create.argtypes = [ctypes.POINTER(vp), i32]
+    L.kc_destroy.restype = None
+    L.kc_destroy.argtypes = [vp]
+    L.kc_sync.restype = st
+    L.kc_sync.argtypes = [vp, vp]
+    L.kc_buf_status.restype = i32
+    L.kc_buf_status.argtypes = [vp, i32]
+    L.kc_set_digest_shape.restype = st
+    L.kc_set_digest_shape.argtypes = [vp, i32, i32, i32]
+    L.kc_set_trace_events.restype = st
+    L.kc_set_trace_events.argtypes = [vp, vp, vp]
+    L.kc_get_digest_shape.restype = st
+    L.kc_get_digest_shape.argtypes = [vp, u32, u64] + [ctypes.POINTER(i32)] * 4
+    L.kc_page_count.restype = u64
+    L.kc_page_count.argtypes = [ctypes.POINTER(KcBuf), i32, u32]
+    B = ctypes.POINTER(KcBuf)
+    L.kc_digest.restype = st
+    L.kc_digest.argtypes = [vp, B, i32, u32, vp, vp, vp, vp]
+    L.kc_census.restype = st
+    L.kc_census.argtypes = [vp, B, i32, u64, u64, vp, u64, vp, vp]
+    L.kc_scan.restype = st
+    L.kc_scan.argtypes = [vp, B, i32, u32, vp, vp, vp, u64, u64, vp, u64, vp, vp]
+    L.kc_dedup.restype = st
+    L.kc_dedup.argtypes = [vp, B, i32, u32, vp, vp, vp, vp, u64, vp, vp]
+    L.kc_restore.restype = st
+    L.kc_restore.argtypes = [vp, B, i32, u32, vp, u64, vp, u64, vp]
+    L.kc_compare.restype = st
+    L.kc_compare.argtypes = [vp, B, B, i32, ctypes.c_double, ctypes.c_double, vp, vp]
+    _lib = L
+    return L
+
+
+def status_name(s: int) -> str:
+    try:
+        return load().kc_status_name(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def bufs(items) -> ctypes.Array:
+    """Array of kc_buf from (base_va, bytes[, dtype[, flags]]) tuples or torch tensors."""
+    arr = (KcBuf * len(items))()
+    for i, it in enumerate(items):
+        if hasattr(it, "data_ptr"):
+            arr[i] = KcBuf(it.data_ptr(), it.numel() * it.element_size(), RAW, 0)
+        else:
+            t = tuple(it) + (RAW, 0)[len(it) - 2:]
+            arr[i] = KcBuf(int(t[0]), int(t[1]), int(t[2]), int(t[3]))
+    return arr
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+class Context:
+    """One kc_ctx on one device; serves one stream at a time."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        s = self.lib.kc_create(ctypes.byref(h), device)
+        if s != OK:
+            raise KcError(s, f"kc_create(device={device}) failed")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.kc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s, allow=(OK, EBUF)):
+        if s not in allow:
+            raise KcError(s, self.lib.kc_last_error(self.h).decode())
+        return s
+
+    def last_error(self) -> str:
+        return self.lib.kc_last_error(self.h).decode()
+
+    def sync(self, stream=None) -> int:
+        """kc_sync: wait, then return the device-side status (raises on none)."""
+        return self.lib.kc_sync(self.h, _stream(stream))
+
+    def buf_status(self, i: int) -> int:
+        return self.lib.kc_buf_status(self.h, i)
+
+    def set_digest_shape(self, warps=0, stages=0, chunk=0):
+        return self._check(self.lib.kc_set_digest_shape(self.h, warps, stages, chunk), (OK,))
+
+    def set_trace_events(self, start=None, stop=None):
+        """Record torch.cuda.Event objects around the main kernel of later calls."""
+        a = start.cuda_event if start is not None else None
+        b = stop.cuda_event if stop is not None else None
+        return self._check(self.lib.kc_set_trace_events(self.h, a, b), (OK,))
+
+    def digest_shape(self, page_bytes: int, npages: int):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(self.lib.kc_get_digest_shape(self.h, page_bytes, npages,
+                                                 *[ctypes.byref(x) for x in v]), (OK,))
+        return dict(warps=v[0].value, stages=v[1].value, chunk=v[2].value, ctas=v[3].value)
+
+    def digest(self, regions, page_bytes, hash_out, zero_out, page_first_out=None, stream=None,
+               allow=(OK, EBUF)):
+        b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+        return self._check(self.lib.kc_digest(self.h, b, len(b), page_bytes, _ptr(hash_out),
+                                              _ptr(zero_out), _ptr(page_first_out),
+                                              _stream(stream)), allow)
+
+    def scan(self, regions, page_bytes, hash_out, zero_out, page_first_out, win_lo, win_hi,
+             hits_out, cap, counts_out, stream=None, allow=(OK, EBUF)):
+        b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+        return self._check(self.lib.kc_scan(self.h, b, len(b), page_bytes, _ptr(hash_out),
+                                            _ptr(zero_out), _ptr(page_first_out), win_lo, win_hi,
+                                            _ptr(hits_out), cap, _ptr(counts_out),
+                                            _stream(stream)), allow)
+
+    def census(self, regions, win_lo, win_hi, hits_out, cap, counts_out, stream=None,
+               allow=(OK, EBUF)):
+        b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+        return self._check(self.lib.kc_census(self.h, b, len(b), win_lo, win_hi, _ptr(hits_out),
+                                              cap, _ptr(counts_out), _stream(stream)), allow)
+
+    def dedup(self, regions, page_bytes, hash_in, zero_in, table_out, arena_out, arena_cap,
+              n_blobs_out, stream=None, allow=(OK, EBUF)):
+        b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+        return self._check(self.lib.kc_dedup(self.h, b, len(b), page_bytes, _ptr(hash_in),
+                                             _ptr(zero_in), _ptr(table_out), _ptr(arena_out),
+                                             arena_cap, _ptr(n_blobs_out), _stream(stream)), allow)
+
+    def restore(self, regions, page_bytes, table, n_pages, arena, arena_bytes, stream=None,
+                allow=(OK, EBUF)):
+        b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+        return self._check(self.lib.kc_restore(self.h, b, len(b), page_bytes, _ptr(table),
+                                               n_pages, _ptr(arena), arena_bytes,
+                                               _stream(stream)), allow)
+
+    def compare(self, got, want, atol, rtol, out, stream=None, allow=(OK, EBUF)):
+        g = got if isinstance(got, ctypes.Array) else bufs(got)
+        w = want if isinstance(want, ctypes.Array) else bufs(want)
+        assert len(g) == len(w)
+        return self._check(self.lib.kc_compare(self.h, g, w, len(g), float(atol), float(rtol),
+                                               _ptr(out), _stream(stream)), allow)
+
+
+def launch_count() -> int:
+    """Kernels launched by libkc.so in this process so far."""
+    return int(load().kc_launch_count())
+
+
+def page_count(regions, page_bytes: int) -> int:
+    b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+    return int(load().kc_page_count(b, len(b), page_bytes))

@@ -1,0 +1,290 @@
+"""GPU parity: every output of the CUDA path, through the C ABI, against the
+CPU oracle on the same seeded inputs.  Integers, hashes, tables, arenas and
+hit lists must be bit-exact; the FP64 error maxima too (they are single IEEE
+operations and order-independent maxima, so the tolerance is zero).
+
+Sizes: the tiny mixed snapshot (16 regions, ~16 MiB, ragged tails) spans
+hundreds of 8-page digest tasks and compare tiles; page sizes 4 KiB..2 MiB
+and forced kernel shapes cover one-stage to deep rings.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_03208_gb300 import kc
+from paper_2605_03208_gb300 import workloads as W
+from tests import _gpu as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    kc.load()
+    c = kc.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    snap, dev = G.device_snapshot(W.tiny_layout(0), W.tiny_fill, 0)
+    return snap, dev
+
+
+def _oracle_digest(snap, S):
+    return oracle.digest(snap.regions, S)
+
+
+# ---------------------------------------------------------------- digest
+
+@pytest.mark.parametrize("S", [4096, 65536, 2 * 1024 * 1024])
+def test_digest_tiny_bit_exact(ctx, tiny, S):
+    snap, dev = tiny
+    st, h, z, pf = G.run_digest(ctx, snap, dev, S)
+    assert st == kc.OK
+    oh, oz, opf = _oracle_digest(snap, S)
+    assert np.array_equal(pf, opf)
+    assert np.array_equal(z, oz)
+    assert np.array_equal(h, oh)
+    assert ctx.sync() == kc.OK
+
+
+@pytest.mark.parametrize("shape", [(1, 2, 256), (2, 3, 512), (4, 4, 1024), (4, 2, 2048), (3, 5, 384),
+                                   (16, 2, 256)])
+def test_digest_forced_shapes(ctx, tiny, shape):
+    snap, dev = tiny
+    ctx.set_digest_shape(*shape)
+    try:
+        st, h, z, pf = G.run_digest(ctx, snap, dev, 65536)
+    finally:
+        ctx.set_digest_shape(0, 0, 0)
+    oh, oz, _ = _oracle_digest(snap, 65536)
+    assert st == kc.OK and np.array_equal(h, oh) and np.array_equal(z, oz)
+
+
+def test_digest_edge_lengths(ctx):
+    sizes = [1, 7, 8, 15, 16, 31, 32, 33, 63, 64, 100, 4095, 4096, 4097, 8191, 12288 + 40, 70000]
+    rng = np.random.default_rng(11)
+    regions = [rng.integers(0, 256, s, dtype=np.uint8) for s in sizes]
+    regions[5][:] = 0                      # an all-zero short page
+    regions[13][4096:8191] = 0             # a zero second page
+    dev = [torch.from_numpy(r).cuda() for r in regions]
+    snap = W.Snapshot("edge", 4096, sizes, [t.data_ptr() for t in dev], regions, [kc.RAW] * len(sizes))
+    for S in (4096, 8192):
+        st, h, z, pf = G.run_digest(ctx, snap, dev, S)
+        oh, oz, opf = _oracle_digest(snap, S)
+        assert st == kc.OK
+        assert np.array_equal(h, oh) and np.array_equal(z, oz) and np.array_equal(pf, opf)
+
+
+# ---------------------------------------------------------------- census
+
+def test_scan_fused_matches_digest_and_census(ctx, tiny):
+    snap, dev = tiny
+    win = W.default_window(snap.bases, snap.sizes)
+    st, r = G.run_scan(ctx, snap, dev, win)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    oh, oz, opf = _oracle_digest(snap, snap.page_bytes)
+    assert np.array_equal(r["hash"], oh) and np.array_equal(r["zero"], oz)
+    hits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert rc == 0
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    n = nin + nout
+    assert G.hits_tuples(r["hits"][:n]) == G.hits_tuples(hits)
+    assert set(snap.truth["pointers"]) <= set(G.hits_tuples(r["hits"][:n]))
+
+
+def test_census_standalone(ctx, tiny):
+    snap, dev = tiny
+    win = W.default_window(snap.bases, snap.sizes)
+    st, hits, counts = G.run_census(ctx, snap, dev, win)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert (int(counts[0]), int(counts[1])) == (nin, nout)
+    assert G.hits_tuples(hits[: nin + nout]) == G.hits_tuples(ohits)
+
+
+def test_census_dense_pointers_and_truncation(ctx):
+    layout = W.tiny_layout(3, n=12, total=6 * W.MiB)
+    snap, dev = G.device_snapshot(layout, W.tiny_fill, 3, p_ptr=0.6, p_zero=0.1)
+    win = W.default_window(snap.bases, snap.sizes)
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert nin + nout > 100000
+    st, hits, counts = G.run_census(ctx, snap, dev, win)
+    assert ctx.sync() == kc.OK
+    assert G.hits_tuples(hits[: nin + nout]) == G.hits_tuples(ohits)
+    cap = 1000
+    st, hits, counts = G.run_census(ctx, snap, dev, win, cap=cap)
+    assert ctx.sync() == kc.ETRUNC
+    assert (int(counts[0]), int(counts[1])) == (nin, nout)
+    assert G.hits_tuples(hits[:cap]) == G.hits_tuples(ohits[:cap])
+    # count-only mode
+    st, _, counts = G.run_census(ctx, snap, dev, win, cap=0)
+    assert ctx.sync() == kc.OK and (int(counts[0]), int(counts[1])) == (nin, nout)
+
+
+# ---------------------------------------------------------------- dedup / restore
+
+def _dedup_vs_oracle(ctx, snap, dev, S, hash_bits=64):
+    oh, oz, _ = _oracle_digest(snap, S)
+    if hash_bits < 64:
+        oh = oh & np.uint64((1 << hash_bits) - 1)
+    # the oracle's digest is the input of both sides
+    h_dev = torch.from_numpy(oh.view(np.int64).copy()).cuda()
+    z_dev = torch.from_numpy(oz.copy()).cuda()
+    st, t, arena, nb = G.run_dedup(ctx, snap, dev, h_dev, z_dev, S)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    ot = oracle.dedup(snap.regions, S, oh, oz)
+    assert nb == ot["n_blobs"]
+    assert np.array_equal(t["va_offset"], ot["off"])
+    assert np.array_equal(t["alloc_id"], ot["alloc"])
+    assert np.array_equal(t["blob"], ot["blob"])
+    oarena = oracle.pack(snap.regions, S, ot)
+    assert np.array_equal(G.to_np(arena)[: nb * S], oarena)
+    return t, arena, nb
+
+
+@pytest.mark.parametrize("S", [4096, 65536])
+def test_dedup_tiny(ctx, tiny, S):
+    snap, dev = tiny
+    _dedup_vs_oracle(ctx, snap, dev, S)
+
+
+@pytest.mark.parametrize("bits", [0, 3, 8])
+def test_dedup_forced_collisions(ctx, tiny, bits):
+    snap, dev = tiny
+    _dedup_vs_oracle(ctx, snap, dev, 65536, hash_bits=bits)
+
+
+def test_dedup_tiled_sort_path(ctx):
+    # > 8192 non-zero pages: the multi-CTA radix sort passes
+    layout = W.tiny_layout(5, n=20, total=48 * W.MiB, page_bytes=4096)
+    snap, dev = G.device_snapshot(layout, W.tiny_fill, 5)
+    assert sum(-(-s // 4096) for s in snap.sizes) > 9000
+    _dedup_vs_oracle(ctx, snap, dev, 4096)
+    _dedup_vs_oracle(ctx, snap, dev, 4096, hash_bits=12)
+
+
+def test_restore_roundtrip(ctx, tiny):
+    snap, dev = tiny
+    S = snap.page_bytes
+    t, arena, nb = _dedup_vs_oracle(ctx, snap, dev, S)
+    table = torch.from_numpy(t.view(np.uint8).copy()).cuda()
+    targets = [torch.full_like(x, 0xA5) for x in dev]
+    b = G.region_bufs(snap, targets)
+    st = ctx.restore(b, S, table, len(t), arena, nb * S)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    for tg, r in zip(targets, snap.regions):
+        assert np.array_equal(G.to_np(tg), r)
+
+
+def test_restore_rejects_bad_rows(ctx, tiny):
+    snap, dev = tiny
+    S = snap.page_bytes
+    targets = [torch.full_like(x, 0xA5) for x in dev[:2]]
+    rows = np.zeros(4, dtype=kc.PAGE_DTYPE)
+    rows[0] = (0, 0, kc.BLOB_ZERO)                 # fine: zeros
+    rows[1] = (0, 7, kc.BLOB_ZERO)                 # region 7 does not exist in this list
+    rows[2] = (1 << 40, 0, kc.BLOB_ZERO)           # offset beyond the region
+    rows[3] = (0, 1, 1000)                         # blob beyond the arena
+    arena = torch.zeros(S, dtype=torch.uint8, device="cuda")
+    b = G.region_bufs(W.Snapshot("x", S, snap.sizes[:2], dtypes=[kc.RAW] * 2), targets)
+    ctx.restore(b, S, torch.from_numpy(rows.view(np.uint8).copy()).cuda(), 4, arena, S)
+    assert ctx.sync() == kc.EINVAL
+    t0 = G.to_np(targets[0])
+    assert (t0[: min(S, t0.size)] == 0).all()
+    assert (G.to_np(targets[1]) == 0xA5).all()
+
+
+# ---------------------------------------------------------------- compare
+
+def _cmp_gpu(ctx, pairs, atol=0.0, rtol=0.0):
+    g = [torch.from_numpy(np.ascontiguousarray(p.got).view(np.uint8)).cuda() for p in pairs]
+    w = [torch.from_numpy(np.ascontiguousarray(p.want).view(np.uint8)).cuda() for p in pairs]
+    gb = kc.bufs([(x.data_ptr(), x.numel(), p.dtype, 0) for x, p in zip(g, pairs)])
+    wb = kc.bufs([(x.data_ptr(), x.numel(), p.dtype, 0) for x, p in zip(w, pairs)])
+    out = torch.empty(len(pairs) * 64, dtype=torch.uint8, device="cuda")
+    st = ctx.compare(gb, wb, atol, rtol, out)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    return G.to_np(out).view(kc.CMP_DTYPE)
+
+
+def _assert_records_equal(got, want):
+    assert got.tobytes() == want.tobytes(), (got, want)
+
+
+def test_compare_tiny_pairs(ctx):
+    pairs = W.tiny_pairs(0)
+    recs = _cmp_gpu(ctx, pairs)
+    for rec, p in zip(recs, pairs):
+        _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_compare_mixed_dtypes_ragged(ctx, seed):
+    pairs = W.mixed_pairs(seed, n_pairs=15, max_elems=300_000)
+    recs = _cmp_gpu(ctx, pairs)
+    for rec, p in zip(recs, pairs):
+        _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype))
+
+
+@pytest.mark.parametrize("atol,rtol", [(1e-7, 0.0), (0.0, 1e-6), (1e-6, 1e-5)])
+def test_compare_tolerances(ctx, atol, rtol):
+    pairs = W.tiny_pairs(1, n=1 << 18)
+    recs = _cmp_gpu(ctx, pairs, atol, rtol)
+    for rec, p in zip(recs, pairs):
+        _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype, atol, rtol))
+
+
+def test_compare_special_values(ctx):
+    inf, nan = np.inf, np.nan
+    g = np.array([0.0, -0.0, inf, inf, -inf, 1.0, nan, nan, 2.0, 3.0, 0.0, 1e-45, 5, 6, 7, 8, 9],
+                 dtype=np.float32)
+    w = np.array([-0.0, 0.0, inf, -inf, 5.0, inf, nan, 1.0, nan, 3.0, 1.0, 0.0, 5, 6, 7, 8, 9.5],
+                 dtype=np.float32)
+    h16 = np.array([0x7C00, 0xFC00, 0x7E00, 0x0001, 0x8000, 0x3C00, 0x7BFF, 0x0400], dtype=np.uint16)
+    w16 = np.array([0x7C00, 0x7C00, 0x7E01, 0x0000, 0x0000, 0x3C01, 0x7BFE, 0x03FF], dtype=np.uint16)
+    pairs = [W.Pair(g, w, W.DT_F32), W.Pair(h16, w16, W.DT_F16), W.Pair(h16, w16, W.DT_BF16),
+             W.Pair(np.array([-2**31, 2**31 - 1, 0, 1], np.int32),
+                    np.array([2**31 - 1, -2**31, 0, 1], np.int32), W.DT_I32)]
+    recs = _cmp_gpu(ctx, pairs, 1e30, 1e30)
+    for rec, p in zip(recs, pairs):
+        _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype, 1e30, 1e30))
+
+
+# ---------------------------------------------------------------- failures
+
+def test_lost_region_does_not_disturb_others(ctx, tiny):
+    snap, dev = tiny
+    flags = [0] * len(dev)
+    flags[3] = kc.BUF_LOST
+    st, h, z, pf = G.run_digest(ctx, snap, dev, 65536, flags=flags)
+    assert st == kc.EBUF
+    assert ctx.buf_status(3) == kc.EBUF and ctx.buf_status(2) == kc.OK
+    oh, oz, opf = _oracle_digest(snap, 65536)
+    lost = np.zeros(len(h), bool)
+    lost[int(opf[3]):int(opf[4])] = True
+    assert (z[lost] == kc.PAGE_LOST).all() and (h[lost] == 0).all()
+    assert np.array_equal(h[~lost], oh[~lost]) and np.array_equal(z[~lost], oz[~lost])
+    # the census skips the lost source but keeps it as a target
+    win = W.default_window(snap.bases, snap.sizes)
+    st, hits, counts = G.run_census(ctx, snap, dev, win, flags=flags)
+    assert st == kc.EBUF and ctx.sync() == kc.OK
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    keep = [x for x in G.hits_tuples(ohits) if x[0] != 3]
+    assert G.hits_tuples(hits[: len(keep)]) == keep
+
+
+def test_argument_errors(ctx, tiny):
+    snap, dev = tiny
+    h = torch.empty(1024, dtype=torch.int64, device="cuda")
+    z = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    bad = kc.bufs([(dev[0].data_ptr() + 8, 100, kc.RAW, 0)])
+    assert ctx.digest(bad, 4096, h, z, allow=range(8)) == kc.EINVAL
+    assert ctx.digest(G.region_bufs(snap, dev), 3000, h, z, allow=range(8)) == kc.EINVAL
+    ov = kc.bufs([(dev[0].data_ptr(), 4096), (dev[0].data_ptr() + 1024, 4096)])
+    counts = torch.zeros(2, dtype=torch.int64, device="cuda")
+    assert ctx.census(ov, 0, 0, None, 0, counts, allow=range(8)) == kc.EOVERLAP
+    assert "overlap" in ctx.last_error()
