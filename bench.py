@@ -313,6 +313,10 @@ def run_kc(args):
     ops = ["scan", "dedup", "restore", "compare"]
     tr = {op: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)] for op in ops}
+    for op in ops:          # torch creates the cudaEvent_t on first record
+        for a, b in tr[op]:
+            a.record(stream)
+            b.record(stream)
     barrier()
     launches0 = kc.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

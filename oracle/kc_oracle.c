@@ -350,16 +350,20 @@ static int cmp_range(const void *a, const void *b) {
 /*
  * Census of embedded device pointers.  Regions are the half-open ranges
  * [base_k, base_k + bytes_k); they must not overlap.  For region i in list
- * order and every offset o = 0, 8, 16, ... with o + 8 <= bytes_i, the word v
+ * order and every offset o = 0, 8, 16, ... with o + 8 <= scan_i, the word v
  * (little-endian u64) is INSIDE when some range holds it (target = that
  * region's list index), else OUTSIDE when win_lo <= v < win_hi (target -1),
- * else not a hit.  Hits are listed in (region, offset) order; at most `cap`
- * are stored, the counts are always the true ones.
- * Returns 0; 2 if the ranges overlap; 4 if hits were truncated; -1 on OOM.
+ * else not a hit.  scan_i = bytes_i unless `scan` is given: a region with a
+ * shorter scan length is still a whole target range but only its first
+ * scan_i bytes (the image provided) are read; scan_i = 0 makes it a target
+ * only, like a region that could not be read.  Hits are listed in (region,
+ * offset) order; at most `cap` are stored, the counts are always the true
+ * ones.  Returns 0; 2 if the ranges overlap; 4 if hits were truncated; -1 on
+ * OOM.
  */
 int kco_census(int n, const uint8_t *const *img, const uint64_t *base, const uint64_t *bytes,
-               uint64_t win_lo, uint64_t win_hi, kco_hit *hits, uint64_t cap,
-               uint64_t *n_inside, uint64_t *n_outside) {
+               const uint64_t *scan, uint64_t win_lo, uint64_t win_hi, kco_hit *hits,
+               uint64_t cap, uint64_t *n_inside, uint64_t *n_outside) {
     kco_range *rg = (kco_range *)malloc(sizeof(kco_range) * (size_t)(n ? n : 1));
     if (!rg) return -1;
     for (int k = 0; k < n; ++k) { rg[k].base = base[k]; rg[k].end = base[k] + bytes[k]; rg[k].id = k; }
@@ -369,7 +373,8 @@ int kco_census(int n, const uint8_t *const *img, const uint64_t *base, const uin
     }
     uint64_t cnt = 0, nin = 0, nout = 0;
     for (int i = 0; i < n; ++i) {
-        for (uint64_t o = 0; o + 8 <= bytes[i]; o += 8) {
+        uint64_t lim = scan ? scan[i] : bytes[i];
+        for (uint64_t o = 0; o + 8 <= lim; o += 8) {
             uint64_t v = le64(img[i] + o);
             /* upper bound: first range whose base is > v */
             int lo = 0, hi = n;

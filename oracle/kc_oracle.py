@@ -68,7 +68,7 @@ def lib():
             L.kco_restore.restype = None
             L.kco_restore.argtypes = [i32, vp, vp, u32, u64, vp, vp, vp, vp]
             L.kco_census.restype = i32
-            L.kco_census.argtypes = [i32, vp, vp, vp, u64, u64, vp, u64, vp, vp]
+            L.kco_census.argtypes = [i32, vp, vp, vp, vp, u64, u64, vp, u64, vp, vp]
             L.kco_compare.restype = None
             L.kco_compare.argtypes = [vp, vp, i32, u64, ctypes.c_double, ctypes.c_double, vp]
             _lib = L
@@ -82,7 +82,8 @@ def _ptr(a: np.ndarray) -> int:
 def _region_table(regions):
     """Return (pointer array, bytes array, keep-alive list) for uint8 regions."""
     keep = [np.ascontiguousarray(r, dtype=np.uint8).reshape(-1) for r in regions]
-    ptrs = np.array([_ptr(r) for r in keep], dtype=np.uint64)
+    keep = [r if r.size else np.zeros(1, np.uint8)[:0] for r in keep]
+    ptrs = np.array([_ptr(r) if r.size else 0 for r in keep], dtype=np.uint64)
     nbytes = np.array([r.size for r in keep], dtype=np.uint64)
     return ptrs, nbytes, keep
 
@@ -161,17 +162,24 @@ def restore(targets, page_bytes: int, table, arena) -> None:
                       _ptr(np.ascontiguousarray(table["blob"], dtype=np.uint32)), _ptr(a))
 
 
-def census(regions, bases, win_lo: int, win_hi: int, cap: int | None = None):
-    """Embedded-pointer census.  Returns (hits structured array, n_inside, n_outside, rc)."""
-    ptrs, nbytes, keep = _region_table(regions)
+def census(regions, bases, win_lo: int, win_hi: int, cap: int | None = None, sizes=None):
+    """Embedded-pointer census.  Returns (hits structured array, n_inside, n_outside, rc).
+
+    ``sizes`` (optional) gives each region's full size as a target range when
+    the image passed in ``regions`` is only its first bytes (possibly none):
+    only the image is scanned.
+    """
+    ptrs, scan, keep = _region_table(regions)
     bases = np.ascontiguousarray(bases, dtype=np.uint64)
+    nbytes = scan if sizes is None else np.ascontiguousarray(sizes, dtype=np.uint64)
+    assert np.all(scan <= nbytes)
     if cap is None:
-        cap = int(sum(int(b) // 8 for b in nbytes))
+        cap = int(sum(int(b) // 8 for b in scan))
     hits = np.zeros(max(cap, 1), dtype=HIT_DTYPE)
     nin = np.zeros(1, dtype=np.uint64)
     nout = np.zeros(1, dtype=np.uint64)
-    rc = lib().kco_census(len(keep), _ptr(ptrs), _ptr(bases), _ptr(nbytes), win_lo, win_hi,
-                          _ptr(hits), cap, _ptr(nin), _ptr(nout))
+    rc = lib().kco_census(len(keep), _ptr(ptrs), _ptr(bases), _ptr(nbytes), _ptr(scan), win_lo,
+                          win_hi, _ptr(hits), cap, _ptr(nin), _ptr(nout))
     if rc == -1:
         raise MemoryError("oracle census out of memory")
     total = int(nin[0] + nout[0])

@@ -199,72 +199,90 @@ __global__ void cmp_init_kernel(const CmpPair *__restrict__ pairs, int npairs, k
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// Merge one CTA's accumulators into the pair's record (all threads call it).
+__device__ void cmp_flush(CmpAcc &acc, kc_cmp_result *o, unsigned long long (*red)[CMP_THREADS / 32]) {
+    unsigned long long v[7] = {acc.mism, acc.first, acc.nan_g, acc.nan_w, acc.nan_m,
+                               dbits(acc.max_abs), dbits(acc.max_rel)};
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+        const unsigned long long f = __shfl_xor_sync(0xffffffffu, v[1], off);
+        v[1] = f < v[1] ? f : v[1];
+        v[2] += __shfl_xor_sync(0xffffffffu, v[2], off);
+        v[3] += __shfl_xor_sync(0xffffffffu, v[3], off);
+        v[4] += __shfl_xor_sync(0xffffffffu, v[4], off);
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, v[5], off);
+        v[5] = a > v[5] ? a : v[5];
+        const unsigned long long r = __shfl_xor_sync(0xffffffffu, v[6], off);
+        v[6] = r > v[6] ? r : v[6];
+    }
+    if (lane_id() == 0) {
+#pragma unroll
+        for (int j = 0; j < 7; ++j) red[j][threadIdx.x >> 5] = v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long sm[7] = {0ull, ~0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+        for (int wi = 0; wi < CMP_THREADS / 32; ++wi) {
+            sm[0] += red[0][wi];
+            sm[1] = red[1][wi] < sm[1] ? red[1][wi] : sm[1];
+            sm[2] += red[2][wi];
+            sm[3] += red[3][wi];
+            sm[4] += red[4][wi];
+            sm[5] = red[5][wi] > sm[5] ? red[5][wi] : sm[5];
+            sm[6] = red[6][wi] > sm[6] ? red[6][wi] : sm[6];
+        }
+        if (sm[0]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->mismatches), sm[0]);
+        if (sm[1] != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(&o->first), sm[1]);
+        if (sm[2]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_got), sm[2]);
+        if (sm[3]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_want), sm[3]);
+        if (sm[4]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_mismatch), sm[4]);
+        if (sm[5]) atomicMax(reinterpret_cast<unsigned long long *>(&o->max_abs), sm[5]);
+        if (sm[6]) atomicMax(reinterpret_cast<unsigned long long *>(&o->max_rel), sm[6]);
+    }
+    __syncthreads();
+    acc = CmpAcc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0};
+}
+
+// Each CTA takes a contiguous range of tiles, so consecutive tiles mostly
+// belong to the same pair and a CTA merges into a pair's record once per
+// pair it touches, not once per tile.
 __global__ void __launch_bounds__(CMP_THREADS) cmp_kernel(const CmpPair *__restrict__ pairs, int npairs,
                                                           uint64_t ntiles, double atol, double rtol,
                                                           kc_cmp_result *__restrict__ out) {
     __shared__ unsigned long long red[7][CMP_THREADS / 32];
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // pair owning this tile: last pair whose first tile <= tile
-        int lo = 0, hi = npairs - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (pairs[mid].tile_first <= tile) lo = mid;
-            else hi = mid - 1;
-        }
-        const CmpPair pr = pairs[lo];
-        CmpAcc acc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0};
-        if (!pr.lost) {
-            const uint64_t tip = tile - pr.tile_first;
-            switch (pr.dtype) {
-            case KC_F32: cmp_tile<KC_F32>(pr, tip, atol, rtol, acc); break;
-            case KC_F16: cmp_tile<KC_F16>(pr, tip, atol, rtol, acc); break;
-            case KC_BF16: cmp_tile<KC_BF16>(pr, tip, atol, rtol, acc); break;
-            case KC_I32: cmp_tile<KC_I32>(pr, tip, atol, rtol, acc); break;
-            default: cmp_tile<KC_U8>(pr, tip, atol, rtol, acc); break;
-            }
-        }
-        unsigned long long v[7] = {acc.mism, acc.first, acc.nan_g, acc.nan_w, acc.nan_m,
-                                   dbits(acc.max_abs), dbits(acc.max_rel)};
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-            unsigned long long f = __shfl_xor_sync(0xffffffffu, v[1], o);
-            v[1] = f < v[1] ? f : v[1];
-            v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
-            v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
-            v[4] += __shfl_xor_sync(0xffffffffu, v[4], o);
-            unsigned long long a = __shfl_xor_sync(0xffffffffu, v[5], o);
-            v[5] = a > v[5] ? a : v[5];
-            unsigned long long r = __shfl_xor_sync(0xffffffffu, v[6], o);
-            v[6] = r > v[6] ? r : v[6];
-        }
-        if (lane_id() == 0) {
-#pragma unroll
-            for (int j = 0; j < 7; ++j) red[j][threadIdx.x >> 5] = v[j];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long s[7] = {0ull, ~0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-            for (int wi = 0; wi < CMP_THREADS / 32; ++wi) {
-                s[0] += red[0][wi];
-                s[1] = red[1][wi] < s[1] ? red[1][wi] : s[1];
-                s[2] += red[2][wi];
-                s[3] += red[3][wi];
-                s[4] += red[4][wi];
-                s[5] = red[5][wi] > s[5] ? red[5][wi] : s[5];
-                s[6] = red[6][wi] > s[6] ? red[6][wi] : s[6];
-            }
-            kc_cmp_result *o = &out[lo];
-            if (s[0]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->mismatches), s[0]);
-            if (s[1] != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(&o->first), s[1]);
-            if (s[2]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_got), s[2]);
-            if (s[3]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_want), s[3]);
-            if (s[4]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_mismatch), s[4]);
-            if (s[5]) atomicMax(reinterpret_cast<unsigned long long *>(&o->max_abs), s[5]);
-            if (s[6]) atomicMax(reinterpret_cast<unsigned long long *>(&o->max_rel), s[6]);
-        }
-        __syncthreads();
+    const uint64_t t0 = ntiles * blockIdx.x / gridDim.x;
+    const uint64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    if (t0 >= t1) return;
+    // pair owning t0: last pair whose first tile <= t0
+    int lo = 0, hi = npairs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pairs[mid].tile_first <= t0) lo = mid;
+        else hi = mid - 1;
     }
+    int k = lo;
+    CmpPair pr = pairs[k];
+    CmpAcc acc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0};
+    for (uint64_t tile = t0; tile < t1; ++tile) {
+        bool moved = false;
+        while (k + 1 < npairs && pairs[k + 1].tile_first <= tile) {
+            if (!moved) cmp_flush(acc, &out[k], red);
+            moved = true;
+            ++k;
+        }
+        if (moved) pr = pairs[k];
+        if (pr.lost) continue;
+        const uint64_t tip = tile - pr.tile_first;
+        switch (pr.dtype) {
+        case KC_F32: cmp_tile<KC_F32>(pr, tip, atol, rtol, acc); break;
+        case KC_F16: cmp_tile<KC_F16>(pr, tip, atol, rtol, acc); break;
+        case KC_BF16: cmp_tile<KC_BF16>(pr, tip, atol, rtol, acc); break;
+        case KC_I32: cmp_tile<KC_I32>(pr, tip, atol, rtol, acc); break;
+        default: cmp_tile<KC_U8>(pr, tip, atol, rtol, acc); break;
+        }
+    }
+    cmp_flush(acc, &out[k], red);
 }
 
 cudaError_t launch_compare(const CmpPair *pairs, int npairs, uint64_t ntiles, double atol, double rtol,

@@ -129,99 +129,260 @@ __global__ void dd_compact_kernel(const uint64_t *__restrict__ hash, const uint3
 __device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 0xffu; }
 
 // Rank ITEMS striped elements of this warp; wcnt = this warp's 256 counters.
+// The lanes sharing a lane's 8-bit digit are found with eight ballots, one
+// per digit bit (a lane's peers agree with it on every bit).
 template <int ITEMS>
 __device__ __forceinline__ void warp_rank(const uint64_t (&key)[ITEMS], int shift, uint32_t *wcnt,
                                           uint16_t (&local)[ITEMS]) {
-    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         const uint32_t d = digit_of(key[r], shift);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = __popc(peers & lanemask_lt());
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        const uint32_t before = __popc(peers & lt);
         const uint32_t base = wcnt[d];
         local[r] = (uint16_t)(base + before);
         __syncwarp();
         if (before == 0) wcnt[d] = base + __popc(peers);
         __syncwarp();
     }
-    (void)lane;
 }
 
-// One CTA sorts up to RS_SMALL keys: registers hold the current order, shared
-// memory receives each pass's scatter.
-__global__ void __launch_bounds__(RS_SMALL_THREADS) rs_small_kernel(const uint64_t *__restrict__ keys_in,
-                                                                    const uint32_t *__restrict__ vals_in,
-                                                                    const uint64_t *__restrict__ m_ptr,
-                                                                    uint64_t *__restrict__ keys_out,
-                                                                    uint32_t *__restrict__ vals_out) {
+// Exclusive scan of 256 digit totals by one warp (8 digits per lane).
+__device__ __forceinline__ void digit_bases(const uint32_t *dsum, uint32_t *dbase) {
+    const int lane = threadIdx.x & 31;
+    uint32_t v[8], loc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        v[j] = dsum[lane * 8 + j];
+        loc += v[j];
+    }
+    uint32_t inc = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    uint32_t run = inc - loc;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        dbase[lane * 8 + j] = run;
+        run += v[j];
+    }
+}
+
+// Block-wide exclusive sum of one u32 per thread; *total gets the sum.
+// `ws` is 32 words of shared scratch.  Every thread must call it.
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t *ws, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = lane < nw ? ws[lane] : 0u;
+        uint32_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        ws[lane] = xi - x;
+        if (lane == 31) ws[32] = xi;
+    }
+    __syncthreads();
+    const uint32_t r = ws[warp] + inc - v;
+    if (total) *total = ws[32];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide inclusive max of one u32 per thread.  `ws`: 33 words of scratch.
+__device__ __forceinline__ uint32_t block_incl_max(uint32_t v, uint32_t *ws) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = y > inc ? y : inc;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = lane < nw ? ws[lane] : 0u;
+        uint32_t xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi = y > xi ? y : xi;
+        }
+        uint32_t ex = __shfl_up_sync(0xffffffffu, xi, 1);
+        ws[lane] = lane ? ex : 0u;
+    }
+    __syncthreads();
+    const uint32_t r = ws[warp] > inc ? ws[warp] : inc;
+    __syncthreads();
+    return r;
+}
+
+// Block-wide exclusive max of one u32 per thread (0 for thread 0).
+__device__ __forceinline__ uint32_t block_excl_max(uint32_t v, uint32_t *ws) {
+    const uint32_t inc = block_incl_max(v, ws);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t prev = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (lane == 0) prev = warp ? ws[warp - 1] : 0u;
+    __syncthreads();
+    return prev;
+}
+
+// ---- small snapshots (P <= RS_SMALL pages): the whole front in one CTA -----
+//
+// Compaction of the non-zero pages, the eight radix passes and the segment
+// scan run in one CTA of 512 threads.  Registers hold the current order
+// (warp-striped: warp w, round r, lane j holds element 512 w + 32 r + j);
+// shared memory receives each pass's stable scatter.
+__global__ void __launch_bounds__(RS_SMALL_THREADS) dd_small_front_kernel(
+    const uint64_t *__restrict__ hash, const uint8_t *__restrict__ zero, uint32_t P,
+    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint64_t *__restrict__ misc,
+    uint32_t *__restrict__ seg, uint32_t *__restrict__ dups) {
     constexpr int NW = RS_SMALL_THREADS / 32;
-    constexpr int PER_WARP = 32 * RS_TILE_ITEMS;
+    constexpr int ITEMS = RS_TILE_ITEMS;
+    constexpr int PER_WARP = 32 * ITEMS;
     extern __shared__ __align__(16) uint8_t sm[];
     uint64_t *sk = reinterpret_cast<uint64_t *>(sm);
     uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_SMALL);
-    uint32_t *cnt = sv + RS_SMALL;              // [NW][256]
-    __shared__ uint32_t dsum[256];
-    __shared__ uint32_t dbase[256];
+    uint32_t *cnt = sv + RS_SMALL;   // [NW][256]
+    __shared__ uint32_t dsum[256], dbase[256], ws[33];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const uint32_t m = (uint32_t)*m_ptr;
-    if (m == 0) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t key[RS_TILE_ITEMS];
-    uint32_t val[RS_TILE_ITEMS];
-    uint16_t loc[RS_TILE_ITEMS];
+    // 1. compaction (blocked: thread t owns pages 16t .. 16t + 15)
+    uint32_t fl = 0, nloc = 0;
 #pragma unroll
-    for (int r = 0; r < RS_TILE_ITEMS; ++r) {
-        const uint32_t i = warp * PER_WARP + r * 32 + lane;
-        key[r] = i < m ? keys_in[i] : ~0ull;
-        val[r] = i < m ? vals_in[i] : 0xffffffffu;
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t p = tid * ITEMS + j;
+        const bool f = p < P && zero[p] == KC_PAGE_DATA;
+        fl |= (uint32_t)f << j;
+        nloc += f;
     }
+    uint32_t m = 0;
+    uint32_t o = block_excl_sum(nloc, ws, &m);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        if ((fl >> j) & 1) {
+            const uint32_t p = tid * ITEMS + j;
+            sk[o] = hash[p];
+            sv[o] = p;
+            ++o;
+        }
+    }
+    __syncthreads();
+    if (m == 0) {
+        if (tid == 0) {
+            misc[0] = 0;
+            misc[2] = 0;
+        }
+        return;
+    }
+
+    // 2. eight stable passes of 8-bit digits
+    uint64_t key[ITEMS];
+    uint32_t val[ITEMS];
+    uint16_t loc[ITEMS];
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+        const uint32_t i = warp * PER_WARP + r * 32 + lane;
+        key[r] = i < m ? sk[i] : ~0ull;   // padding sorts last and is never written
+        val[r] = i < m ? sv[i] : 0xffffffffu;
+    }
+    __syncthreads();
     for (int shift = 0; shift < 64; shift += 8) {
-        for (int i = threadIdx.x; i < NW * 256; i += blockDim.x) cnt[i] = 0;
+        for (int i = tid; i < NW * 256; i += blockDim.x) cnt[i] = 0;
         __syncthreads();
-        warp_rank<RS_TILE_ITEMS>(key, shift, cnt + warp * 256, loc);
+        warp_rank<ITEMS>(key, shift, cnt + warp * 256, loc);
         __syncthreads();
-        if (threadIdx.x < 256) {
-            const int d = threadIdx.x;
+        {   // per digit, exclusive over warps: two threads per digit, 8 warps each
+            const int d = tid & 255, h = tid >> 8;
             uint32_t run = 0;
-            for (int w = 0; w < NW; ++w) {
+            for (int w = h * (NW / 2); w < (h + 1) * (NW / 2); ++w) {
                 const uint32_t t = cnt[w * 256 + d];
                 cnt[w * 256 + d] = run;
                 run += t;
             }
-            dsum[d] = run;
+            if (h == 0) dsum[d] = run;
+            __syncthreads();
+            if (h == 1) {
+                const uint32_t lo = dsum[d];
+                for (int w = NW / 2; w < NW; ++w) cnt[w * 256 + d] += lo;
+                dbase[d] = lo + run;        // digit total, scanned below
+            }
+            __syncthreads();
+            if (h == 0) dsum[d] = dbase[d];
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t run = 0;
-            for (int d = 0; d < 256; ++d) {
-                dbase[d] = run;
-                run += dsum[d];
+        if (tid < 32) digit_bases(dsum, dbase);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) {
+            const uint32_t d = digit_of(key[r], shift);
+            const uint32_t at = dbase[d] + cnt[warp * 256 + d] + loc[r];
+            sk[at] = key[r];
+            sv[at] = val[r];
+        }
+        __syncthreads();
+        if (shift < 56) {
+#pragma unroll
+            for (int r = 0; r < ITEMS; ++r) {
+                const uint32_t i = warp * PER_WARP + r * 32 + lane;
+                key[r] = sk[i];
+                val[r] = sv[i];
+            }
+            __syncthreads();
+        }
+    }
+
+    // 3. output, segment starts (max-scan of head indices), equal-hash neighbours
+    uint32_t hmax = 0, nd = 0, dfl = 0;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t i = tid * ITEMS + j;
+        if (i < m) {
+            keys_out[i] = sk[i];
+            vals_out[i] = sv[i];
+            const bool head = i == 0 || sk[i] != sk[i - 1];
+            if (head) hmax = i;
+            else {
+                dfl |= 1u << j;
+                ++nd;
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < RS_TILE_ITEMS; ++r) {
-            const uint32_t d = digit_of(key[r], shift);
-            const uint32_t o = dbase[d] + cnt[warp * 256 + d] + loc[r];
-            sk[o] = key[r];
-            sv[o] = val[r];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < RS_TILE_ITEMS; ++r) {
-            const uint32_t i = warp * PER_WARP + r * 32 + lane;
-            key[r] = sk[i];
-            val[r] = sv[i];
-        }
-        __syncthreads();
     }
+    uint32_t run = block_excl_max(hmax, ws);
+    uint32_t ndup = 0;
+    uint32_t dpos = block_excl_sum(nd, ws, &ndup);
 #pragma unroll
-    for (int r = 0; r < RS_TILE_ITEMS; ++r) {
-        const uint32_t i = warp * PER_WARP + r * 32 + lane;
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t i = tid * ITEMS + j;
         if (i < m) {
-            keys_out[i] = key[r];
-            vals_out[i] = val[r];
+            if (!((dfl >> j) & 1)) run = i;
+            seg[i] = run;
+            if ((dfl >> j) & 1) dups[dpos++] = i;
         }
+    }
+    if (tid == 0) {
+        misc[0] = m;
+        misc[2] = ndup;
     }
 }
 
@@ -525,6 +686,102 @@ __global__ void dd_table_kernel(Pages pg, const uint8_t *__restrict__ zero, cons
     }
 }
 
+// ---- small snapshots: classes, slow path, blob ids and the table in one CTA -----
+
+constexpr int SMALL_BACK_THREADS = 1024;
+
+__global__ void __launch_bounds__(SMALL_BACK_THREADS) dd_small_back_kernel(
+    Pages pg, const uint8_t *__restrict__ zero, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ seg, const uint32_t *__restrict__ dups, const uint32_t *__restrict__ neq,
+    uint64_t *__restrict__ misc, uint32_t *__restrict__ reps, kc_page *__restrict__ table,
+    uint32_t *__restrict__ blob_page, uint64_t *__restrict__ n_blobs_out) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    uint32_t *bad = reinterpret_cast<uint32_t *>(sm);   // [RS_SMALL] per sorted position
+    uint32_t *canon = bad + RS_SMALL;                   // [RS_SMALL] per page
+    uint32_t *list = canon + RS_SMALL;                  // [RS_SMALL] bad segments, then blob ids
+    __shared__ uint32_t ws[33];
+    __shared__ uint32_t nbad;
+    const int tid = threadIdx.x;
+    const uint32_t m = (uint32_t)misc[0], ndup = (uint32_t)misc[2], P = (uint32_t)pg.npages;
+    for (uint32_t i = tid; i < m; i += blockDim.x) bad[i] = 0;
+    for (uint32_t p = tid; p < P; p += blockDim.x) canon[p] = p;
+    if (tid == 0) nbad = 0;
+    __syncthreads();
+    for (uint32_t j = tid; j < ndup; j += blockDim.x) {
+        const uint32_t i = dups[j];
+        if (neq[i]) {
+            const uint32_t s = seg[i];
+            if (atomicExch(&bad[s], 1u) == 0u) list[atomicAdd(&nbad, 1u)] = s;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < m; i += blockDim.x) {
+        const uint32_t s = seg[i];
+        if (!bad[s]) canon[vals[i]] = vals[s];
+    }
+    __syncthreads();
+    const uint32_t nb_seg = nbad;
+    for (uint32_t b = 0; b < nb_seg; ++b) {       // rare: hash collisions only
+        const uint32_t s = list[b];
+        uint32_t nrep = 0;
+        for (uint32_t j = s; j < m && seg[j] == s; ++j) {
+            const uint32_t pj = vals[j];
+            uint32_t found = 0xffffffffu;
+            for (uint32_t r = 0; r < nrep; ++r) {
+                if (cta_pages_equal(pg, pj, reps[s + r])) {
+                    found = reps[s + r];
+                    break;
+                }
+            }
+            if (tid == 0) {
+                if (found != 0xffffffffu) canon[pj] = found;
+                else {
+                    reps[s + nrep] = pj;
+                    canon[pj] = pj;
+                }
+            }
+            if (found == 0xffffffffu) ++nrep;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // blob ids: exclusive scan of "canonical non-zero page" in page order
+    constexpr int PER = RS_SMALL / SMALL_BACK_THREADS;
+    uint32_t fl = 0, nloc = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint32_t p = tid * PER + j;
+        const bool f = p < P && zero[p] == KC_PAGE_DATA && canon[p] == p;
+        fl |= (uint32_t)f << j;
+        nloc += f;
+    }
+    uint32_t nb = 0;
+    uint32_t o = block_excl_sum(nloc, ws, &nb);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        if ((fl >> j) & 1) {
+            const uint32_t p = tid * PER + j;
+            list[p] = o;
+            blob_page[o] = p;
+            ++o;
+        }
+    }
+    __syncthreads();
+    for (uint32_t p = tid; p < P; p += blockDim.x) {
+        const int a = region_of(pg.regions, pg.nregions, p);
+        kc_page row;
+        row.va_offset = (p - pg.regions[a].first) << pg.log2page;
+        row.alloc_id = (uint32_t)a;
+        const uint8_t z = zero[p];
+        row.blob = z == KC_PAGE_ZERO ? KC_BLOB_ZERO : z == KC_PAGE_LOST ? KC_BLOB_LOST : list[canon[p]];
+        table[p] = row;
+    }
+    if (tid == 0) {
+        misc[1] = nb;
+        if (n_blobs_out) *n_blobs_out = nb;
+    }
+}
+
 // ---- 6. pack ----------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) dd_pack_kernel(Pages pg, const uint32_t *__restrict__ blob_page,
@@ -570,6 +827,14 @@ __global__ void __launch_bounds__(256) dd_pack_kernel(Pages pg, const uint32_t *
 
 // ---- driver ------------------------------------------------------------------------
 
+cudaError_t setup_dedup_kernels() {
+    const size_t fsm = (size_t)RS_SMALL * 12 + (RS_SMALL_THREADS / 32) * 256 * 4;
+    cudaError_t e = cudaFuncSetAttribute(dd_small_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(dd_small_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(RS_SMALL * 12));
+}
+
 static inline unsigned grid_for(uint64_t n, int threads, int sms, int per_sm) {
     uint64_t b = (n + threads - 1) / threads;
     const uint64_t cap = (uint64_t)sms * per_sm;
@@ -590,6 +855,24 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
     const unsigned g = grid_for(P, 256, sms, 8);
     KC_TRY(cudaMemsetAsync(s.misc, 0, 64, st));
     KC_TRY(cudaMemsetAsync(s.neq, 0, P * 4, st));
+    const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
+    if (P <= (uint64_t)RS_SMALL) {
+        // small: front (compaction + sort + segments) and back (classes +
+        // blob ids + table) run in one CTA each, around the wide verify
+        const size_t fsm = (size_t)RS_SMALL * 12 + (RS_SMALL_THREADS / 32) * 256 * 4;
+        dd_small_front_kernel<<<1, RS_SMALL_THREADS, fsm, st>>>(hash, zero, (uint32_t)P, s.keys[0], s.vals[0], s.misc,
+                                                                s.seg, s.dups);
+        count_launches(1);
+        KC_TRY(cudaGetLastError());
+        dd_verify_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.vals[0], s.dups, s.misc, s.neq);
+        count_launches(1);
+        KC_TRY(cudaGetLastError());
+        const size_t bsm = (size_t)RS_SMALL * 12;
+        dd_small_back_kernel<<<1, SMALL_BACK_THREADS, bsm, st>>>(pg, zero, s.vals[0], s.seg, s.dups, s.neq, s.misc,
+                                                                 s.reps, table, s.blob_page, n_blobs);
+        count_launches(1);
+        KC_TRY(cudaGetLastError());
+    } else {
     KC_TRY(cudaMemsetAsync(s.bad, 0, P * 4, st));
     // 1. compaction
     dd_flag_kernel<<<g, 256, 0, st>>>(zero, P, s.flags);
@@ -599,14 +882,8 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
     dd_compact_kernel<<<g, 256, 0, st>>>(hash, s.flags, s.pos, P, s.keys[0], s.vals[0]);
     count_launches(1);
     KC_TRY(cudaGetLastError());
-    // 2. sort (m <= P)
-    if (P <= (uint64_t)RS_SMALL) {
-        const size_t smem = (size_t)RS_SMALL * 12 + (RS_SMALL_THREADS / 32) * 256 * 4;
-        KC_TRY(cudaFuncSetAttribute(rs_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        rs_small_kernel<<<1, RS_SMALL_THREADS, smem, st>>>(s.keys[0], s.vals[0], &s.misc[0], s.keys[0], s.vals[0]);
-        count_launches(1);
-        KC_TRY(cudaGetLastError());
-    } else {
+    // 2. sort: tiled passes
+    {
         const uint32_t ntiles = (uint32_t)ceil_div(P, RS_TILE);
         int src = 0;
         for (int shift = 0; shift < 64; shift += 8) {
@@ -627,7 +904,6 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
     dd_segments_kernel<<<1, SEG_THREADS, 0, st>>>(s.keys[0], s.misc, s.seg, s.dups);
     count_launches(1);
     KC_TRY(cudaGetLastError());
-    const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
     dd_verify_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.vals[0], s.dups, s.misc, s.neq);
     count_launches(1);
     KC_TRY(cudaGetLastError());
@@ -650,6 +926,7 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
     count_launches(1);
     KC_TRY(cudaGetLastError());
     if (n_blobs) KC_TRY(cudaMemcpyAsync(n_blobs, &s.misc[1], 8, cudaMemcpyDeviceToDevice, st));
+    }
     // 6. pack
     if (arena) {
         dd_pack_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.blob_page, s.misc, arena,

@@ -1,5 +1,6 @@
 // k_digest.cu -- page digest (XXH64 seed 0 + zero flag), optionally fused
-// with the pointer-census count, and the census count / write / scan kernels.
+// with the pointer-census pre-filter, and the census count / write / scan
+// kernels.
 //
 // Digest mapping.  XXH64 keeps four serial accumulators, one per 8-byte lane
 // of every 32-byte stripe, so one page is hashed by a quad of four threads
@@ -14,6 +15,16 @@
 // spread over all 32 banks.  The < 32-byte tail of a page (and the < 16-byte
 // part a bulk copy cannot move) is read from global memory by the quad
 // leader while it finishes the hash.
+//
+// The serial chain per accumulator is the critical path: each step is an
+// add, a rotate and a multiply by PRIME1 (xx_step); the lane products
+// (lane * PRIME2) and the next stripes' shared loads are issued ahead of it.
+//
+// Census when fused: the hashing loop only keeps, per page, the minimum of
+// (high 32 bits of a word - pre_lo), a branch-free conservative test of
+// whether any word can be a hit.  Pages that pass are classified afterwards
+// by census_flagged_kernel, one word per lane, so a pointer-dense page never
+// holds up the hashing warps.
 #include <cuda_runtime.h>
 
 #include "kc_device.cuh"
@@ -22,6 +33,9 @@
 namespace kc {
 
 static __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// page_hits value of a page whose words must still be classified
+constexpr uint32_t HITS_PENDING = 0xFFFFFFFFu;
 
 size_t digest_smem_bytes(const DigestShape &s) {
     size_t bars = align_up((size_t)s.warps * s.stages * sizeof(uint64_t), 128);
@@ -33,10 +47,8 @@ template <bool CENSUS>
 __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, uint64_t *__restrict__ hash,
                                                      uint8_t *__restrict__ zero,
                                                      uint32_t *__restrict__ page_hits,
-                                                     uint64_t *__restrict__ counts,
                                                      uint32_t *__restrict__ task_ctr,
-                                                     uint32_t *__restrict__ status, int stages,
-                                                     int chunk) {
+                                                     uint32_t *__restrict__ status, int stages, int chunk) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
@@ -66,13 +78,12 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
         const bool valid = p < pg.npages;
 
         const uint8_t *src = nullptr;
-        uint64_t len = 0, off = 0;
-        uint32_t region = 0;
+        uint64_t len = 0;
         bool lost = false;
         if (valid) {
-            region = (uint32_t)region_of(pg.regions, pg.nregions, p);
+            const int region = region_of(pg.regions, pg.nregions, p);
             const Region r = pg.regions[region];
-            off = (p - r.first) << pg.log2page;
+            const uint64_t off = (p - r.first) << pg.log2page;
             len = r.bytes - off < pg.page ? r.bytes - off : pg.page;
             src = reinterpret_cast<const uint8_t *>(r.base + off);
             lost = r.lost != 0;
@@ -104,8 +115,8 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
         for (uint32_t c = 0; c < pre; ++c) issue(c);
 
         uint64_t acc = xx_init(k);
-        uint64_t zor = 0;
-        uint32_t hin = 0, hout = 0;
+        uint32_t zlo = 0, zhi = 0;
+        uint32_t cmin = 0xFFFFFFFFu;   // census pre-filter, minimum over the page
         bool timed_out = false;
         uint32_t c = 0;
         for (; c < maxch; ++c) {
@@ -124,37 +135,45 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
             }
             const uint8_t *slot = ring + st * stage_stride + q * slot_stride + 8 * k;
             uint32_t s = 0;
-            for (; s + 128 <= b; s += 128) {
-                uint64_t w0 = *reinterpret_cast<const uint64_t *>(slot + s);
-                uint64_t w1 = *reinterpret_cast<const uint64_t *>(slot + s + 32);
-                uint64_t w2 = *reinterpret_cast<const uint64_t *>(slot + s + 64);
-                uint64_t w3 = *reinterpret_cast<const uint64_t *>(slot + s + 96);
-                acc = xx_round(acc, w0);
-                acc = xx_round(acc, w1);
-                acc = xx_round(acc, w2);
-                acc = xx_round(acc, w3);
-                zor |= (w0 | w1) | (w2 | w3);
-                if (CENSUS) {
-                    int32_t tg;
-                    uint64_t ws[4] = {w0, w1, w2, w3};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        int cl = census_classify(ca, ws[u], &tg);
-                        hin += cl == 1;
-                        hout += cl == 2;
+            if (b >= 128) {
+                // register double buffer: the next four stripes are loaded
+                // while the current four run through the chain
+                uint64_t w0 = *reinterpret_cast<const uint64_t *>(slot);
+                uint64_t w1 = *reinterpret_cast<const uint64_t *>(slot + 32);
+                uint64_t w2 = *reinterpret_cast<const uint64_t *>(slot + 64);
+                uint64_t w3 = *reinterpret_cast<const uint64_t *>(slot + 96);
+                for (; s + 128 <= b; s += 128) {
+                    const uint32_t ns = (s + 256 <= b) ? s + 128 : s;   // last group reloads itself
+                    const uint64_t n0 = *reinterpret_cast<const uint64_t *>(slot + ns);
+                    const uint64_t n1 = *reinterpret_cast<const uint64_t *>(slot + ns + 32);
+                    const uint64_t n2 = *reinterpret_cast<const uint64_t *>(slot + ns + 64);
+                    const uint64_t n3 = *reinterpret_cast<const uint64_t *>(slot + ns + 96);
+                    const uint64_t m0 = w0 * XXP2, m1 = w1 * XXP2, m2 = w2 * XXP2, m3 = w3 * XXP2;
+                    acc = xx_step(acc, m0);
+                    acc = xx_step(acc, m1);
+                    acc = xx_step(acc, m2);
+                    acc = xx_step(acc, m3);
+                    zlo |= (uint32_t)w0 | (uint32_t)w1 | (uint32_t)w2 | (uint32_t)w3;
+                    zhi |= (uint32_t)(w0 >> 32) | (uint32_t)(w1 >> 32) | (uint32_t)(w2 >> 32) |
+                           (uint32_t)(w3 >> 32);
+                    if (CENSUS) {
+                        cmin = min(cmin, census_pre(ca, w0));
+                        cmin = min(cmin, census_pre(ca, w1));
+                        cmin = min(cmin, census_pre(ca, w2));
+                        cmin = min(cmin, census_pre(ca, w3));
                     }
+                    w0 = n0;
+                    w1 = n1;
+                    w2 = n2;
+                    w3 = n3;
                 }
             }
             for (; s < b; s += 32) {
-                uint64_t w = *reinterpret_cast<const uint64_t *>(slot + s);
-                acc = xx_round(acc, w);
-                zor |= w;
-                if (CENSUS) {
-                    int32_t tg;
-                    int cl = census_classify(ca, w, &tg);
-                    hin += cl == 1;
-                    hout += cl == 2;
-                }
+                const uint64_t w = *reinterpret_cast<const uint64_t *>(slot + s);
+                acc = xx_step(acc, w * XXP2);
+                zlo |= (uint32_t)w;
+                zhi |= (uint32_t)(w >> 32);
+                if (CENSUS) cmin = min(cmin, census_pre(ca, w));
             }
             __syncwarp();
             if (c + stages < maxch) issue(c + stages);
@@ -172,18 +191,17 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
         }
         pos += maxch;
 
-        // Quad reduction: accumulators to the quad leader, OR of bytes, hit counts.
+        // Quad reduction: accumulators to the quad leader, OR of bytes, census flag.
         const int qb = lane & ~3;
         const uint64_t a1 = __shfl_sync(FULL, acc, qb + 1);
         const uint64_t a2 = __shfl_sync(FULL, acc, qb + 2);
         const uint64_t a3 = __shfl_sync(FULL, acc, qb + 3);
+        uint64_t zor = ((uint64_t)zhi << 32) | zlo;
         zor |= __shfl_xor_sync(FULL, zor, 1);
         zor |= __shfl_xor_sync(FULL, zor, 2);
         if (CENSUS) {
-            hin += __shfl_xor_sync(FULL, hin, 1);
-            hin += __shfl_xor_sync(FULL, hin, 2);
-            hout += __shfl_xor_sync(FULL, hout, 1);
-            hout += __shfl_xor_sync(FULL, hout, 2);
+            cmin = min(cmin, __shfl_xor_sync(FULL, cmin, 1));
+            cmin = min(cmin, __shfl_xor_sync(FULL, cmin, 2));
         }
         if (k == 0 && valid) {
             if (lost) {
@@ -204,20 +222,13 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
                 h += len;
                 const uint8_t *tp = src + sbytes;
                 uint32_t rem = (uint32_t)(len - sbytes);
-                uint64_t toff = off + sbytes;
                 while (rem >= 8) {
                     const uint64_t w = ldg_u64(tp);
                     h ^= xx_round(0, w);
                     h = rotl(h, 27) * XXP1 + XXP4;
                     zor |= w;
-                    if (CENSUS) {
-                        int32_t tg;
-                        int cl = census_classify(ca, w, &tg);
-                        hin += cl == 1;
-                        hout += cl == 2;
-                    }
+                    if (CENSUS) cmin = min(cmin, census_pre(ca, w));
                     tp += 8;
-                    toff += 8;
                     rem -= 8;
                 }
                 if (rem >= 4) {
@@ -243,54 +254,166 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
                 h ^= h >> 32;
                 hash[p] = h;
                 zero[p] = zor == 0 ? KC_PAGE_ZERO : KC_PAGE_DATA;
-                if (CENSUS) {
-                    page_hits[p] = hin + hout;
-                    if (hin) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), hin);
-                    if (hout) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), hout);
-                }
+                if (CENSUS) page_hits[p] = (cmin <= ca.pre_span && len >= 8) ? HITS_PENDING : 0u;
             }
         }
     }
 }
 
+cudaError_t setup_digest_kernels() {
+    const int max_smem = 227 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(digest_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(digest_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+// ---- census: classification of flagged units ------------------------------------
+//
+// A unit (a page, or a 64 KiB census chunk) is split between the 8 warps of
+// a CTA, each taking a contiguous run of its words; a warp walks its run 256
+// words per step (8 loads in flight per lane), each lane classifying its
+// words against the ranges held in shared memory.  Counting needs no order;
+// writing places each hit at the unit's offset plus the hits of the warps
+// before it (a scan of the warps' counts) plus the hits before it in the
+// warp (ballot ranks), i.e. in word order.
+
+constexpr int CENSUS_THREADS = 256;
+constexpr int CENSUS_WARPS = CENSUS_THREADS / 32;
+
+// Hits among words [wb, we) of a unit; with `hits`, they are written from
+// index `out` on (indices >= cap are dropped).
+__device__ __forceinline__ void warp_census_range(const CensusArgs &ca, const Range *rg, const uint8_t *base,
+                                                  uint64_t wb, uint64_t we, uint64_t unit_off, uint32_t region,
+                                                  kc_hit *hits, uint64_t out, uint64_t cap, uint32_t &nin,
+                                                  uint32_t &nout) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    nin = 0;
+    nout = 0;
+    for (uint64_t w0 = wb; w0 < we; w0 += 256) {
+        uint64_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint64_t w = w0 + 32 * j + lane;
+            v[j] = w < we ? ldg_u64(base + 8 * w) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint64_t w = w0 + 32 * j + lane;
+            int cl = 0;
+            int32_t tg = -1;
+            if (w < we && census_pre(ca, v[j]) <= ca.pre_span) cl = census_classify(ca, rg, v[j], &tg);
+            const uint32_t bin = __ballot_sync(0xffffffffu, cl == 1);
+            const uint32_t bout = __ballot_sync(0xffffffffu, cl == 2);
+            if (hits && cl) {
+                const uint64_t idx = out + nin + nout + __popc((bin | bout) & lt);
+                if (idx < cap) {
+                    kc_hit h;
+                    h.src_offset = unit_off + 8 * w;
+                    h.value = v[j];
+                    h.src_alloc = region;
+                    h.target = tg;
+                    hits[idx] = h;
+                }
+            }
+            nin += __popc(bin);
+            nout += __popc(bout);
+        }
+    }
+}
+
+struct UnitSpan {
+    const uint8_t *base;
+    uint64_t off, nwords;
+    int region;
+};
+
+__device__ __forceinline__ UnitSpan unit_span(const Pages &u, uint64_t unit) {
+    UnitSpan s;
+    s.region = region_of(u.regions, u.nregions, unit);
+    const Region r = u.regions[s.region];
+    s.off = (unit - r.first) << u.log2page;
+    const uint64_t len = r.bytes - s.off < u.page ? r.bytes - s.off : u.page;
+    s.base = reinterpret_cast<const uint8_t *>(r.base + s.off);
+    s.nwords = len >> 3;
+    return s;
+}
+
+// Count the hits of every unit whose page_hits entry is HITS_PENDING.
+__global__ void __launch_bounds__(CENSUS_THREADS) census_flagged_kernel(Pages u, CensusArgs ca,
+                                                                         uint32_t *__restrict__ unit_hits,
+                                                                         uint64_t *__restrict__ counts) {
+    __shared__ Range srg[SMEM_RANGES];
+    __shared__ uint32_t red_in[CENSUS_WARPS], red_out[CENSUS_WARPS];
+    const Range *rg = stage_ranges(ca, srg);
+    const int warp = threadIdx.x >> 5;
+    for (uint64_t unit = blockIdx.x; unit < u.npages; unit += gridDim.x) {
+        if (unit_hits[unit] != HITS_PENDING) continue;   // uniform across the CTA
+        const UnitSpan sp = unit_span(u, unit);
+        const uint64_t per = (sp.nwords + CENSUS_WARPS - 1) / CENSUS_WARPS;
+        const uint64_t wb = per * warp, we = wb + per < sp.nwords ? wb + per : sp.nwords;
+        uint32_t nin = 0, nout = 0;
+        if (wb < we) warp_census_range(ca, rg, sp.base, wb, we, sp.off, (uint32_t)sp.region, nullptr, 0, 0, nin, nout);
+        if (lane_id() == 0) {
+            red_in[warp] = nin;
+            red_out[warp] = nout;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t si = 0, so = 0;
+            for (int w = 0; w < CENSUS_WARPS; ++w) {
+                si += red_in[w];
+                so += red_out[w];
+            }
+            unit_hits[unit] = si + so;
+            if (si) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), (unsigned long long)si);
+            if (so) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), (unsigned long long)so);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_census_flagged(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits, uint64_t *counts,
+                                  int sms, cudaStream_t st) {
+    uint64_t blocks = units.npages;
+    const uint64_t maxb = (uint64_t)sms * 8;
+    if (blocks > maxb) blocks = maxb;
+    if (blocks == 0) return cudaSuccess;
+    census_flagged_kernel<<<(unsigned)blocks, CENSUS_THREADS, 0, st>>>(units, ca, unit_hits, counts);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash, uint8_t *zero,
                           uint32_t *page_hits, uint64_t *counts, uint32_t *task_ctr, uint32_t *status,
                           const DigestShape &shape, cudaStream_t st) {
+    (void)counts;
     const size_t smem = digest_smem_bytes(shape);
     const dim3 block(32 * shape.warps), grid(shape.ctas);
-    cudaError_t e;
     if (census) {
-        e = cudaFuncSetAttribute(digest_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        digest_kernel<true><<<grid, block, smem, st>>>(pg, *census, hash, zero, page_hits, counts,
-                                                       task_ctr, status, shape.stages, shape.chunk);
+        digest_kernel<true><<<grid, block, smem, st>>>(pg, *census, hash, zero, page_hits, task_ctr, status,
+                                                       shape.stages, shape.chunk);
         count_launches(1);
     } else {
-        e = cudaFuncSetAttribute(digest_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
         CensusArgs none{};
-        digest_kernel<false><<<grid, block, smem, st>>>(pg, none, hash, zero, nullptr, nullptr,
-                                                        task_ctr, status, shape.stages, shape.chunk);
+        digest_kernel<false><<<grid, block, smem, st>>>(pg, none, hash, zero, nullptr, task_ctr, status,
+                                                        shape.stages, shape.chunk);
         count_launches(1);
     }
     return cudaGetLastError();
 }
 
-// ---- census: count pass ---------------------------------------------------------
+// ---- census: standalone count pass ---------------------------------------------------
 //
-// Units are fixed-size chunks of the regions (the page size for the fused
-// path, 64 KiB for the standalone call).  One CTA counts one unit with
-// 16-byte streaming loads and writes the unit's hit count; nothing else is
-// written, so the scan over units can place every unit's hits in order.
+// Units are 64 KiB chunks of the regions.  One CTA counts one unit with
+// 16-byte streaming loads; candidates (rare unless the data holds pointers)
+// are classified against the ranges in shared memory.
 
-constexpr int CENSUS_THREADS = 256;
-
-__device__ __forceinline__ void census_word(const CensusArgs &ca, uint64_t v, uint32_t &hin,
+__device__ __forceinline__ void census_word(const CensusArgs &ca, const Range *rg, uint64_t v, uint32_t &hin,
                                             uint32_t &hout) {
+    if (census_pre(ca, v) > ca.pre_span) return;
     int32_t tg;
-    int cl = census_classify(ca, v, &tg);
+    const int cl = census_classify(ca, rg, v, &tg);
     hin += cl == 1;
     hout += cl == 2;
 }
@@ -298,7 +421,9 @@ __device__ __forceinline__ void census_word(const CensusArgs &ca, uint64_t v, ui
 __global__ void __launch_bounds__(CENSUS_THREADS) census_count_kernel(Pages u, CensusArgs ca,
                                                                       uint32_t *__restrict__ unit_hits,
                                                                       uint64_t *__restrict__ counts) {
+    __shared__ Range srg[SMEM_RANGES];
     __shared__ uint32_t red_in[CENSUS_THREADS / 32], red_out[CENSUS_THREADS / 32];
+    const Range *rg = stage_ranges(ca, srg);
     for (uint64_t unit = blockIdx.x; unit < u.npages; unit += gridDim.x) {
         const int a = region_of(u.regions, u.nregions, unit);
         const Region r = u.regions[a];
@@ -316,16 +441,16 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_count_kernel(Pages u, C
                 for (int j = 0; j < 4; ++j) v[j] = ldg_stream(base + 16 * (i + j * CENSUS_THREADS));
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    census_word(ca, ((uint64_t)v[j].y << 32) | v[j].x, hin, hout);
-                    census_word(ca, ((uint64_t)v[j].w << 32) | v[j].z, hin, hout);
+                    census_word(ca, rg, ((uint64_t)v[j].y << 32) | v[j].x, hin, hout);
+                    census_word(ca, rg, ((uint64_t)v[j].w << 32) | v[j].z, hin, hout);
                 }
             }
             for (; i < nvec; i += CENSUS_THREADS) {
-                uint4 v = ldg_stream(base + 16 * i);
-                census_word(ca, ((uint64_t)v.y << 32) | v.x, hin, hout);
-                census_word(ca, ((uint64_t)v.w << 32) | v.z, hin, hout);
+                const uint4 v = ldg_stream(base + 16 * i);
+                census_word(ca, rg, ((uint64_t)v.y << 32) | v.x, hin, hout);
+                census_word(ca, rg, ((uint64_t)v.w << 32) | v.z, hin, hout);
             }
-            if ((nwords & 1) && threadIdx.x == 0) census_word(ca, ldg_u64(base + 8 * (nwords - 1)), hin, hout);
+            if ((nwords & 1) && threadIdx.x == 0) census_word(ca, rg, ldg_u64(base + 8 * (nwords - 1)), hin, hout);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -344,15 +469,15 @@ __global__ void __launch_bounds__(CENSUS_THREADS) census_count_kernel(Pages u, C
                 so += red_out[w];
             }
             unit_hits[unit] = si + so;
-            if (si) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), si);
-            if (so) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), so);
+            if (si) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), (unsigned long long)si);
+            if (so) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), (unsigned long long)so);
         }
         __syncthreads();
     }
 }
 
-cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
-                                uint64_t *counts, int sms, cudaStream_t st) {
+cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits, uint64_t *counts,
+                                int sms, cudaStream_t st) {
     uint64_t blocks = units.npages;
     const uint64_t maxb = (uint64_t)sms * 8;
     if (blocks > maxb) blocks = maxb;
@@ -364,69 +489,55 @@ cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32
 
 // ---- census: ordered write pass ---------------------------------------------------
 //
-// One warp per unit that holds hits: it walks the unit's words in order,
-// 32 at a time, and places each hit at unit_off[unit] + (hits before it in
-// the unit), using a ballot for the in-warp rank.  Only units with hits are
-// read again.
+// One CTA per unit that holds hits: a counting pass per warp, a scan of the
+// warps' counts, then the writing pass.  Only units with hits are read
+// again (the second walk mostly hits L2).
 
-__global__ void __launch_bounds__(256) census_write_kernel(Pages u, CensusArgs ca,
-                                                           const uint32_t *__restrict__ unit_hits,
-                                                           const uint64_t *__restrict__ unit_off,
-                                                           kc_hit *__restrict__ hits, uint64_t cap,
-                                                           uint32_t *__restrict__ status) {
-    const uint32_t lane = lane_id();
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw_total = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t unit = gw; unit < u.npages; unit += nw_total) {
+__global__ void __launch_bounds__(CENSUS_THREADS) census_write_kernel(Pages u, CensusArgs ca,
+                                                                      const uint32_t *__restrict__ unit_hits,
+                                                                      const uint64_t *__restrict__ unit_off,
+                                                                      kc_hit *__restrict__ hits, uint64_t cap,
+                                                                      uint32_t *__restrict__ status) {
+    __shared__ Range srg[SMEM_RANGES];
+    __shared__ uint32_t wcount[CENSUS_WARPS];
+    const Range *rg = stage_ranges(ca, srg);
+    const int warp = threadIdx.x >> 5;
+    for (uint64_t unit = blockIdx.x; unit < u.npages; unit += gridDim.x) {
         const uint32_t cnt = unit_hits[unit];
-        if (cnt == 0) continue;
-        const int a = region_of(u.regions, u.nregions, unit);
-        const Region r = u.regions[a];
-        const uint64_t off = (unit - r.first) << u.log2page;
-        const uint64_t len = r.bytes - off < u.page ? r.bytes - off : u.page;
-        const uint8_t *base = reinterpret_cast<const uint8_t *>(r.base + off);
-        const uint64_t nwords = len >> 3;
-        const uint64_t out = unit_off[unit];
-        uint32_t written = 0;
-        for (uint64_t w0 = 0; w0 < nwords; w0 += 32) {
-            const uint64_t w = w0 + lane;
-            int cl = 0;
-            int32_t tg = -1;
-            uint64_t v = 0;
-            if (w < nwords) {
-                v = ldg_u64(base + 8 * w);
-                cl = census_classify(ca, v, &tg);
-            }
-            const uint32_t bal = __ballot_sync(0xffffffffu, cl != 0);
-            if (cl) {
-                const uint64_t idx = out + written + __popc(bal & lanemask_lt());
-                if (idx < cap) {
-                    kc_hit h;
-                    h.src_offset = off + 8 * w;
-                    h.value = v;
-                    h.src_alloc = (uint32_t)a;
-                    h.target = tg;
-                    hits[idx] = h;
-                }
-            }
-            written += __popc(bal);
+        if (cnt == 0) continue;   // uniform across the CTA
+        const UnitSpan sp = unit_span(u, unit);
+        const uint64_t per = (sp.nwords + CENSUS_WARPS - 1) / CENSUS_WARPS;
+        const uint64_t wb = per * warp, we = wb + per < sp.nwords ? wb + per : sp.nwords;
+        uint32_t nin = 0, nout = 0;
+        if (wb < we) warp_census_range(ca, rg, sp.base, wb, we, sp.off, (uint32_t)sp.region, nullptr, 0, 0, nin, nout);
+        if (lane_id() == 0) wcount[warp] = nin + nout;
+        __syncthreads();
+        uint64_t before = 0, total = 0;
+        for (int w = 0; w < CENSUS_WARPS; ++w) {
+            if (w < warp) before += wcount[w];
+            total += wcount[w];
         }
-        if (lane == 0) {
-            if (written != cnt) set_status(status, ST_INTERNAL);
+        const uint64_t out = unit_off[unit];
+        if (wb < we)
+            warp_census_range(ca, rg, sp.base, wb, we, sp.off, (uint32_t)sp.region, hits, out + before, cap, nin,
+                              nout);
+        if (threadIdx.x == 0) {
+            if (total != cnt) set_status(status, ST_INTERNAL);
             if (out + cnt > cap) set_status(status, ST_TRUNC);
         }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca, const uint32_t *unit_hits,
-                                const uint64_t *unit_off, kc_hit *hits, uint64_t cap, uint32_t *status,
-                                int sms, cudaStream_t st) {
-    uint64_t warps = units.npages;
-    uint64_t blocks = (warps + 7) / 8;
-    uint64_t maxb = (uint64_t)sms * 8;
+                                const uint64_t *unit_off, kc_hit *hits, uint64_t cap, uint32_t *status, int sms,
+                                cudaStream_t st) {
+    uint64_t blocks = units.npages;
+    const uint64_t maxb = (uint64_t)sms * 8;
     if (blocks > maxb) blocks = maxb;
     if (blocks == 0) return cudaSuccess;
-    census_write_kernel<<<(unsigned)blocks, 256, 0, st>>>(units, ca, unit_hits, unit_off, hits, cap, status);
+    census_write_kernel<<<(unsigned)blocks, CENSUS_THREADS, 0, st>>>(units, ca, unit_hits, unit_off, hits, cap,
+                                                                     status);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -456,17 +567,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_u32_kernel(const uint32_t *
         uint64_t incl = local;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
         if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            uint64_t ws = warp_sum[lane];
+            const uint64_t ws = warp_sum[lane];
             uint64_t wi = ws;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                const uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
                 if (lane >= o) wi += y;
             }
             warp_sum[lane] = wi - ws;   // exclusive prefix of warps
@@ -485,8 +596,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_u32_kernel(const uint32_t *
     if (tid == 0 && total) *total = carry_s;
 }
 
-cudaError_t launch_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t *total,
-                            cudaStream_t st) {
+cudaError_t launch_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t *total, cudaStream_t st) {
     scan_u32_kernel<<<1, SCAN_THREADS, 0, st>>>(in, out, n, total);
     count_launches(1);
     return cudaGetLastError();

@@ -120,21 +120,22 @@ __device__ __forceinline__ int region_of(const Region *r, int n, uint64_t u) {
 
 // ---- census classification ---------------------------------------------------
 
-// Classify word v: 0 = not a hit, 1 = inside (target in *tgt), 2 = outside.
-__device__ __forceinline__ int census_classify(const CensusArgs &ca, uint64_t v, int32_t *tgt) {
-    bool in_span = (v - ca.span_lo) < ca.span_len;
-    bool in_win = (v - ca.win_lo) < ca.win_len;
+// Classify word v against the sorted ranges `rg` (shared or global memory):
+// 0 = not a hit, 1 = inside (target in *tgt), 2 = outside.
+__device__ __forceinline__ int census_classify(const CensusArgs &ca, const Range *rg, uint64_t v, int32_t *tgt) {
+    const bool in_span = (v - ca.span_lo) < ca.span_len;
+    const bool in_win = (v - ca.win_lo) < ca.win_len;
     if (!(in_span || in_win)) return 0;
     if (in_span) {
         // first range with base > v, then check the one before it
         int lo = 0, hi = ca.nranges;
         while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (ldg_u64(&ca.ranges[mid].base) <= v) lo = mid + 1;
+            const int mid = (lo + hi) >> 1;
+            if (rg[mid].base <= v) lo = mid + 1;
             else hi = mid;
         }
-        if (lo > 0 && v < ldg_u64(&ca.ranges[lo - 1].end)) {
-            *tgt = __ldg(&ca.ranges[lo - 1].id);
+        if (lo > 0 && v < rg[lo - 1].end) {
+            *tgt = rg[lo - 1].id;
             return 1;
         }
     }
@@ -143,6 +144,23 @@ __device__ __forceinline__ int census_classify(const CensusArgs &ca, uint64_t v,
         return 2;
     }
     return 0;
+}
+
+// Ranges held in shared memory by the census kernels when they fit.
+constexpr int SMEM_RANGES = 1024;
+
+// Copy the ranges into `buf` (SMEM_RANGES entries) if they fit; every thread
+// of the CTA must call it.  Returns the array to search.
+__device__ __forceinline__ const Range *stage_ranges(const CensusArgs &ca, Range *buf) {
+    if (ca.nranges > SMEM_RANGES) return ca.ranges;
+    for (int i = threadIdx.x; i < ca.nranges; i += blockDim.x) buf[i] = ca.ranges[i];
+    __syncthreads();
+    return buf;
+}
+
+// Conservative pre-filter: can v be a census hit at all?
+__device__ __forceinline__ uint32_t census_pre(const CensusArgs &ca, uint64_t v) {
+    return (uint32_t)(v >> 32) - ca.pre_lo;   // candidate iff result <= ca.pre_span
 }
 
 // ---- XXH64 (public xxHash specification) -------------------------------------
@@ -158,6 +176,26 @@ __device__ __forceinline__ uint64_t rotl(uint64_t x, int r) { return (x << r) | 
 // Accumulator step for one 8-byte lane of a stripe.
 __device__ __forceinline__ uint64_t xx_round(uint64_t acc, uint64_t lane) {
     return rotl(acc + lane * XXP2, 31) * XXP1;
+}
+
+// The same step with the lane product m = lane * PRIME2 already computed, in
+// 32-bit PTX: only the add, the rotate and the multiply by PRIME1 depend on
+// the previous accumulator, so the lane products of later stripes can be
+// computed while this chain runs.
+__device__ __forceinline__ uint64_t xx_step(uint64_t acc, uint64_t m) {
+    uint32_t olo, ohi;
+    asm("{\n\t.reg .u32 tl, th, rl, rh, h1, h2;\n\t"
+        "add.cc.u32 tl, %2, %4;\n\t"
+        "addc.u32 th, %3, %5;\n\t"
+        "shf.l.wrap.b32 rh, tl, th, 31;\n\t"
+        "shf.l.wrap.b32 rl, th, tl, 31;\n\t"
+        "mul.lo.u32 %0, rl, 0x85EBCA87;\n\t"
+        "mul.hi.u32 h1, rl, 0x85EBCA87;\n\t"
+        "mad.lo.u32 h2, rl, 0x9E3779B1, h1;\n\t"
+        "mad.lo.u32 %1, rh, 0x85EBCA87, h2;\n\t}"
+        : "=r"(olo), "=r"(ohi)
+        : "r"((uint32_t)acc), "r"((uint32_t)(acc >> 32)), "r"((uint32_t)m), "r"((uint32_t)(m >> 32)));
+    return ((uint64_t)ohi << 32) | olo;
 }
 
 // Seed-0 start value of accumulator k (0..3).

@@ -37,11 +37,15 @@ struct Range {
 
 // Census parameters: a word v is a candidate iff it lies in the captured
 // span [span_lo, span_lo + span_len) or the window [win_lo, win_lo + win_len).
+// pre_lo / pre_span: a cheap conservative pre-filter on the high 32 bits of
+// a word -- every candidate satisfies (hi32(v) - pre_lo) <= pre_span
+// (unsigned); pre_span = 0xFFFFFFFF disables it.
 struct CensusArgs {
     const Range *ranges;
     int nranges;
     uint64_t span_lo, span_len;
     uint64_t win_lo, win_len;
+    uint32_t pre_lo, pre_span;
 };
 
 // Work description shared by the page-granular kernels.
@@ -68,15 +72,25 @@ size_t digest_smem_bytes(const DigestShape &s);
 void count_launches(uint64_t n);
 uint64_t launches_so_far();
 
+// One-time per-process kernel attributes (maximum dynamic shared memory).
+cudaError_t setup_kernels();
+cudaError_t setup_digest_kernels();
+cudaError_t setup_dedup_kernels();
+
 // Launchers (each returns the cudaError_t of its launch).
-// `census` NULL: digest only.  Otherwise page_hits[P] and counts[2]
-// ({inside, outside}, zeroed by the caller) receive the census counts.
+// `census` NULL: digest only.  Otherwise page_hits[P] receives 0 for pages
+// that cannot hold a census hit and a pending mark for the others, which
+// launch_census_flagged then resolves.
 cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash,
                           uint8_t *zero, uint32_t *page_hits, uint64_t *counts,
                           uint32_t *task_ctr, uint32_t *status, const DigestShape &shape,
                           cudaStream_t st);
 cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
                                 uint64_t *counts, int sms, cudaStream_t st);
+// Classify the units the fused digest flagged (page_hits == pending):
+// exact per-unit hit counts, totals added to counts[2].
+cudaError_t launch_census_flagged(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
+                                  uint64_t *counts, int sms, cudaStream_t st);
 cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca,
                                 const uint32_t *unit_hits, const uint64_t *unit_off,
                                 kc_hit *hits, uint64_t cap, uint32_t *status, int sms,
@@ -128,6 +142,6 @@ struct CmpPair {
 cudaError_t launch_compare(const CmpPair *pairs, int npairs, uint64_t ntiles, double atol,
                            double rtol, kc_cmp_result *out, const int32_t *init_status,
                            int sms, cudaStream_t st);
-constexpr uint32_t CMP_TILE_BYTES = 64 * 1024;
+constexpr uint32_t CMP_TILE_BYTES = 16 * 1024;
 
 }  // namespace kc

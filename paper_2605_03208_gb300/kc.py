@@ -182,7 +182,13 @@ class Context:
         return self._check(self.lib.kc_set_digest_shape(self.h, warps, stages, chunk), (OK,))
 
     def set_trace_events(self, start=None, stop=None):
-        """Record torch.cuda.Event objects around the main kernel of later calls."""
+        """Record torch.cuda.Event objects around the main kernel of later calls.
+
+        torch creates the underlying cudaEvent_t on first record; a never
+        recorded event is recorded once here so that it exists."""
+        for e in (start, stop):
+            if e is not None and not e.cuda_event:
+                e.record()
         a = start.cuda_event if start is not None else None
         b = stop.cuda_event if stop is not None else None
         return self._check(self.lib.kc_set_trace_events(self.h, a, b), (OK,))

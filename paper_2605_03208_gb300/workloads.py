@@ -320,3 +320,84 @@ def mixed_pairs(seed: int = 0, n_pairs: int = 10, max_elems: int = 50_000):
             got[idx] = want[idx] ^ np.uint8(1)
         out.append(Pair(got, want, dt, dict(perturbed=idx)))
     return out
+
+
+# --------------------------------------------------------------------------
+# MoE weight pool: 64 experts x 24 layers x 20 MiB of bf16 in one region
+# --------------------------------------------------------------------------
+
+MOE_EXPERTS, MOE_LAYERS, MOE_EXPERT_BYTES = 64, 24, 20 * MiB
+
+
+def moe_snapshot(seed: int = 0, experts: int = MOE_EXPERTS, layers: int = MOE_LAYERS,
+                 expert_bytes: int = MOE_EXPERT_BYTES, dup_frac: float = 0.02,
+                 page_bytes: int = 2 * MiB, device: str = "cuda"):
+    """Generate the pool on the device with torch's seeded generator.
+
+    Region 0: the pool, experts x layers x expert_bytes of bf16 ~ N(0, 0.02)
+    with no exact zeros; dup_frac of its pages are then overwritten with
+    exact copies of other (never overwritten) pages.  Region 1: the int64
+    indirection array of every expert's base VA.  Returns (Snapshot without
+    host regions, [pool, ptrs] device tensors, truth).
+    """
+    import torch
+    n_exp = experts * layers
+    pool_bytes = n_exp * expert_bytes
+    pool = torch.empty(pool_bytes, dtype=torch.uint8, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    view = pool.view(torch.bfloat16)
+    step = 256 * MiB // 2
+    tiny = torch.tensor(2.0 ** -120, dtype=torch.bfloat16, device=device)
+    for s in range(0, view.numel(), step):
+        x = torch.randn(min(step, view.numel() - s), generator=g, device=device) * 0.02
+        x = x.to(torch.bfloat16)
+        x = torch.where(x == 0, tiny, x)
+        view[s:s + x.numel()] = x
+        del x
+    npages = pool_bytes // page_bytes
+    rng = np.random.default_rng(seed + 404)
+    ndup = int(round(npages * dup_frac))
+    perm = rng.permutation(npages)
+    dst = np.sort(perm[:ndup])
+    src = rng.choice(perm[ndup:], ndup, replace=True)
+    pv = pool.view(npages, page_bytes)
+    for d, s_ in zip(dst.tolist(), src.tolist()):
+        pv[d].copy_(pv[s_])
+    base = pool.data_ptr()
+    vals = np.array([base + e * expert_bytes for e in range(n_exp)], dtype=np.uint64)
+    ptrs = torch.from_numpy(vals.view(np.int64).copy()).to(device)
+    torch.cuda.synchronize()
+    snap = Snapshot(f"moe-pool-{experts}x{layers}x{expert_bytes // MiB}MiB", page_bytes,
+                    [pool_bytes, ptrs.numel() * 8], [base, ptrs.data_ptr()], [],
+                    [DT_BF16, DT_RAW])
+    snap.truth = dict(dup_dst=dst, dup_src=src, pointers=[(1, 8 * e, int(v), 0)
+                                                          for e, v in enumerate(vals)])
+    return snap, [pool, ptrs]
+
+
+def moe_pairs(seed: int = 0, rows: int = 4096, cols: int = 7168, device: str = "cuda"):
+    """bf16 [rows, cols] ~ N(0, 1): one identical pair and one pair with 0.1% of
+    elements times (1 +- 1e-2) (a step of one ulp where that rounds away).
+    Returns [(got, want, truth)] as device tensors."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed + 505)
+    want = torch.randn(rows * cols, generator=g, device=device).to(torch.bfloat16)
+    want2 = torch.randn(rows * cols, generator=g, device=device).to(torch.bfloat16)
+    rng = np.random.default_rng(seed + 506)
+    n = rows * cols
+    idx = np.sort(rng.choice(n, n // 1000, replace=False))
+    ti = torch.from_numpy(idx).to(device)
+    sign = torch.from_numpy(np.where(rng.random(idx.size) < 0.5, -1.0, 1.0)).to(device)
+    x = want[ti]
+    y = (x.double() * (1.0 + sign * 1e-2)).to(torch.bfloat16)
+    same = y == x
+    if bool(same.any()):
+        bits = x.view(torch.int16)
+        y = torch.where(same, (bits + 1).view(torch.bfloat16), y)
+    got = want.clone()
+    got[ti] = y
+    torch.cuda.synchronize()
+    return [(want2.clone(), want2, dict(perturbed=np.zeros(0, np.int64))),
+            (got, want, dict(perturbed=idx))]

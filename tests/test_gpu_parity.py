@@ -160,7 +160,7 @@ def test_dedup_forced_collisions(ctx, tiny, bits):
 
 def test_dedup_tiled_sort_path(ctx):
     # > 8192 non-zero pages: the multi-CTA radix sort passes
-    layout = W.tiny_layout(5, n=20, total=48 * W.MiB, page_bytes=4096)
+    layout = W.tiny_layout(5, n=40, total=64 * W.MiB, page_bytes=4096)
     snap, dev = G.device_snapshot(layout, W.tiny_fill, 5)
     assert sum(-(-s // 4096) for s in snap.sizes) > 9000
     _dedup_vs_oracle(ctx, snap, dev, 4096)
@@ -288,3 +288,52 @@ def test_argument_errors(ctx, tiny):
     counts = torch.zeros(2, dtype=torch.int64, device="cuda")
     assert ctx.census(ov, 0, 0, None, 0, counts, allow=range(8)) == kc.EOVERLAP
     assert "overlap" in ctx.last_error()
+
+
+# ---------------------------------------------------------------- graphs
+
+def test_graph_capture_replays_bit_exact(ctx, tiny):
+    """After one uncaptured call of each shape, the calls capture into a CUDA
+    graph (no table upload, no scratch growth) and the replay reproduces the
+    oracle's results."""
+    snap, dev = tiny
+    S = snap.page_bytes
+    b = G.region_bufs(snap, dev)
+    P = kc.page_count(b, S)
+    win = W.default_window(snap.bases, snap.sizes)
+    cap = sum(int(s) // 8 for s in snap.sizes)
+    h = torch.empty(P, dtype=torch.int64, device="cuda")
+    z = torch.empty(P, dtype=torch.uint8, device="cuda")
+    pf = torch.empty(len(dev) + 1, dtype=torch.int64, device="cuda")
+    hits = torch.empty(cap * 24, dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(2, dtype=torch.int64, device="cuda")
+    table = torch.empty(P * 16, dtype=torch.uint8, device="cuda")
+    arena = torch.empty(P * S, dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    targets = [torch.full_like(x, 0xA5) for x in dev]
+    tb = G.region_bufs(snap, targets)
+
+    def step():
+        ctx.scan(b, S, h, z, pf, win[0], win[1], hits, cap, counts)
+        ctx.dedup(b, S, h, z, table, arena, P * S, nb)
+        ctx.restore(tb, S, table, P, arena, P * S)
+
+    step()
+    assert ctx.sync() == kc.OK
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for t in (h, z, table, arena, nb, counts):
+        t.zero_()
+    for t in targets:
+        t.fill_(0xA5)
+    g.replay()
+    torch.cuda.synchronize()
+    assert ctx.sync() == kc.OK
+    oh, oz, _ = oracle.digest(snap.regions, S)
+    assert np.array_equal(G.to_np(h).view(np.uint64), oh) and np.array_equal(G.to_np(z), oz)
+    ot = oracle.dedup(snap.regions, S, oh, oz)
+    assert int(G.to_np(nb).view(np.uint64)[0]) == ot["n_blobs"]
+    assert np.array_equal(G.to_np(table).view(kc.PAGE_DTYPE)["blob"], ot["blob"])
+    for tg, r in zip(targets, snap.regions):
+        assert np.array_equal(G.to_np(tg), r)
