@@ -212,6 +212,29 @@ KC_API kc_status kc_digest(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t pa
 KC_API kc_status kc_census(kc_ctx *ctx, const kc_buf *allocs, int n, uint64_t win_lo, uint64_t win_hi,
                     kc_hit *d_hits, uint64_t cap, uint64_t *d_counts, void *stream);
 
+/* kc_census_static: kc_census for callers that must not allocate memory.
+ * The paper has no counterpart; this entry point exists because some
+ * callers cannot call cudaMalloc (or any allocating routine): a hook running
+ * inside the application's allocator or memory-tracking callback, a handler
+ * snapshotting device memory after a failure, or a process whose device
+ * memory is fully reserved.  It computes exactly what kc_census computes on
+ * the caller's current device, with no context, and allocates nothing: its
+ * scratch (region table, sorted ranges, per-64-KiB-chunk hit counts and
+ * offsets, a status word) is one static device array of about 0.8 MiB in
+ * the library image, which every GPU that loads the library holds until the
+ * process exits.  Limits: n <= 1024 regions and at most 65536 chunks of
+ * 64 KiB (ceil(bytes / 64 KiB) summed over the regions, i.e. about 4 GiB);
+ * larger requests return KC_EINVAL before any work.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * it before any stream capture.  Every call on a device shares the array and
+ * overwrites the previous call's contents: calls that may overlap on the GPU
+ * (different streams, or different host threads with unordered streams)
+ * race, so serialise them.  Truncation is not reported separately: the true
+ * counts are written to d_counts, so n_inside + n_outside > cap means the
+ * list was cut.  Returns KC_OK, KC_EINVAL, KC_EOVERLAP, KC_ECUDA or KC_EBUF. */
+KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, uint64_t win_hi,
+                                  kc_hit *d_hits, uint64_t cap, uint64_t *d_counts, void *stream);
+
 /* kc_scan: kc_digest and kc_census fused into one read of the snapshot
  * (the census is counted while pages are hashed, then only pages that hold
  * hits are read a second time to write them in order).  Outputs and errors

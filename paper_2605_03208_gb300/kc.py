@@ -31,7 +31,8 @@ ESIZE = {U8: 1, RAW: 1, I32: 4, F16: 2, BF16: 2, F32: 4}
 # Names declared in include/kc.h (the ABI surface).
 EXPORTS = ["kc_version", "kc_launch_count", "kc_status_name", "kc_last_error", "kc_create", "kc_destroy", "kc_sync",
            "kc_buf_status", "kc_set_digest_shape", "kc_set_trace_events", "kc_get_digest_shape", "kc_page_count",
-           "kc_digest", "kc_census", "kc_scan", "kc_dedup", "kc_restore", "kc_compare"]
+           "kc_digest", "kc_census", "kc_scan", "kc_dedup", "kc_restore", "kc_compare",
+           "kc_census_static"]
 
 
 class KcBuf(ctypes.Structure):
@@ -92,6 +93,8 @@ def load(build_if_missing: bool = False):
     L.kc_digest.argtypes = [vp, B, i32, u32, vp, vp, vp, vp]
     L.kc_census.restype = st
     L.kc_census.argtypes = [vp, B, i32, u64, u64, vp, u64, vp, vp]
+    L.kc_census_static.restype = st
+    L.kc_census_static.argtypes = [B, i32, u64, u64, vp, u64, vp, vp]
     L.kc_scan.restype = st
     L.kc_scan.argtypes = [vp, B, i32, u32, vp, vp, vp, u64, u64, vp, u64, vp, vp]
     L.kc_dedup.restype = st
@@ -240,6 +243,14 @@ class Context:
         assert len(g) == len(w)
         return self._check(self.lib.kc_compare(self.h, g, w, len(g), float(atol), float(rtol),
                                                _ptr(out), _stream(stream)), allow)
+
+
+def census_static(regions, win_lo, win_hi, hits_out, cap, counts_out, stream=None) -> int:
+    """kc_census_static: the census without a context and without allocating
+    (scratch in a static device array; see include/kc.h).  Returns the status."""
+    b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+    return int(load().kc_census_static(b, len(b), win_lo, win_hi, _ptr(hits_out), cap,
+                                       _ptr(counts_out), _stream(stream)))
 
 
 def launch_count() -> int:
