@@ -162,14 +162,15 @@ KC_API int kc_buf_status(const kc_ctx *ctx, int i);
 
 /* kc_set_digest_shape: pin the digest kernel's launch shape for this
  * context: `warps` per CTA (1..16), ring `stages` per warp (2..8), `chunk`
- * bytes per page per stage (multiple of 128, 256..8192).  All three 0
- * restores the built-in choice.  The shape changes speed only, never
- * results.  KC_EINVAL if out of range.
+ * bytes per page per stage (multiple of 128, 256..8192), and `lanes` XXH64
+ * accumulators per thread (1: 4 threads and 8 pages per warp; 2: 2 threads
+ * and 16 pages per warp).  All four 0 restores the built-in choice.  The
+ * shape changes speed only, never results.  KC_EINVAL if out of range.
  * kc_get_digest_shape: the shape a digest of `npages` pages of
  * `page_bytes` would use now, and its grid size (`ctas`). */
-KC_API kc_status kc_set_digest_shape(kc_ctx *ctx, int warps, int stages, int chunk);
+KC_API kc_status kc_set_digest_shape(kc_ctx *ctx, int warps, int stages, int chunk, int lanes);
 KC_API kc_status kc_get_digest_shape(kc_ctx *ctx, uint32_t page_bytes, uint64_t npages, int *warps,
-                                     int *stages, int *chunk, int *ctas);
+                                     int *stages, int *chunk, int *ctas, int *lanes);
 
 /* kc_set_trace_events: `start` and `stop` (cudaEvent_t, or NULL to turn
  * tracing off) are recorded on the call's stream around the main kernel of

@@ -4,9 +4,13 @@
 // non-zero pages m, of equal-hash neighbours, of bad segments, of blobs --
 // stays in device memory and is read by the kernels themselves):
 //   1. compact the non-zero pages into (hash, page id) pairs, page order;
-//   2. stable LSD radix sort on the 64-bit hash, 8-bit digits, 8 passes:
-//      equal hashes end up adjacent, in increasing page id;
-//   3. segments = runs of equal hash; every element that has an equal-hash
+//   2. stable LSD radix sort on the low SORT_BITS = 32 bits of the hash,
+//      8-bit digits, 4 passes: equal hashes end up adjacent, in increasing
+//      page id (two different hashes that share their low 32 bits may
+//      interleave; their segment then fails verification and takes the
+//      slow path below, which decides by bytes alone, so the result is the
+//      same as a sort on all 64 bits);
+//   3. segments = runs of equal sort key; every element that has an equal-key
 //      predecessor is byte-compared with it (16 KiB pieces, one warp each);
 //   4. a segment whose elements all equal their predecessors is one class,
 //      canonical = its first (smallest) page id; any other segment (a hash
@@ -29,6 +33,9 @@ constexpr int RS_TILE = RS_TILE_THREADS * RS_TILE_ITEMS;      // 4096 keys per t
 constexpr int RS_SMALL_THREADS = 512;
 constexpr int RS_SMALL = RS_SMALL_THREADS * RS_TILE_ITEMS;    // 8192 keys, one CTA
 constexpr uint32_t DD_PIECE = 16 * 1024;
+constexpr int SORT_BITS = 32;   // bits of the hash the radix sort orders by
+
+__device__ __forceinline__ uint32_t sort_key(uint64_t k) { return (uint32_t)k; }
 
 static inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
@@ -249,7 +256,7 @@ __device__ __forceinline__ uint32_t block_excl_max(uint32_t v, uint32_t *ws) {
 
 // ---- small snapshots (P <= RS_SMALL pages): the whole front in one CTA -----
 //
-// Compaction of the non-zero pages, the eight radix passes and the segment
+// Compaction of the non-zero pages, the radix passes and the segment
 // scan run in one CTA of 512 threads.  Registers hold the current order
 // (warp-striped: warp w, round r, lane j holds element 512 w + 32 r + j);
 // shared memory receives each pass's stable scatter.
@@ -307,7 +314,7 @@ __global__ void __launch_bounds__(RS_SMALL_THREADS) dd_small_front_kernel(
         val[r] = i < m ? sv[i] : 0xffffffffu;
     }
     __syncthreads();
-    for (int shift = 0; shift < 64; shift += 8) {
+    for (int shift = 0; shift < SORT_BITS; shift += 8) {
         for (int i = tid; i < NW * 256; i += blockDim.x) cnt[i] = 0;
         __syncthreads();
         warp_rank<ITEMS>(key, shift, cnt + warp * 256, loc);
@@ -341,7 +348,7 @@ __global__ void __launch_bounds__(RS_SMALL_THREADS) dd_small_front_kernel(
             sv[at] = val[r];
         }
         __syncthreads();
-        if (shift < 56) {
+        if (shift + 8 < SORT_BITS) {
 #pragma unroll
             for (int r = 0; r < ITEMS; ++r) {
                 const uint32_t i = warp * PER_WARP + r * 32 + lane;
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(RS_SMALL_THREADS) dd_small_front_kernel(
         if (i < m) {
             keys_out[i] = sk[i];
             vals_out[i] = sv[i];
-            const bool head = i == 0 || sk[i] != sk[i - 1];
+            const bool head = i == 0 || sort_key(sk[i]) != sort_key(sk[i - 1]);
             if (head) hmax = i;
             else {
                 dfl |= 1u << j;
@@ -481,7 +488,7 @@ __global__ void __launch_bounds__(SEG_THREADS) dd_segments_kernel(const uint64_t
         const uint64_t i = b + tid;
         uint32_t head_idx = 0, dup = 0;
         if (i < m) {
-            const bool head = (i == 0) || keys[i] != keys[i - 1];
+            const bool head = (i == 0) || sort_key(keys[i]) != sort_key(keys[i - 1]);
             head_idx = head ? (uint32_t)i : 0u;
             dup = head ? 0u : 1u;
         }
@@ -886,7 +893,7 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
     {
         const uint32_t ntiles = (uint32_t)ceil_div(P, RS_TILE);
         int src = 0;
-        for (int shift = 0; shift < 64; shift += 8) {
+        for (int shift = 0; shift < SORT_BITS; shift += 8) {
             rs_hist_kernel<<<ntiles, RS_TILE_THREADS, 0, st>>>(s.keys[src], &s.misc[0], shift, s.hist, ntiles);
             count_launches(1);
             KC_TRY(cudaGetLastError());
@@ -898,7 +905,7 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
             KC_TRY(cudaGetLastError());
             src ^= 1;
         }
-        // eight passes: the result is back in buffer 0
+        // an even number of passes: the result is back in buffer 0
     }
     // 3. segments, neighbours, verification
     dd_segments_kernel<<<1, SEG_THREADS, 0, st>>>(s.keys[0], s.misc, s.seg, s.dups);

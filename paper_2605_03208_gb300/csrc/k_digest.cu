@@ -8,13 +8,15 @@
 // quad) and takes its next eight pages from a global ticket counter, so
 // warps that finish early steal the remaining work.  Each warp owns a ring of
 // `stages` shared-memory stages; a stage holds one `chunk` of each of its
-// eight pages, fetched by one bulk copy (cp.async.bulk, the TMA's 1-D form)
-// per page that completes on the stage's mbarrier.  The first thread of each
-// quad issues its page's copy, so a stage barrier expects eight arrivals.
-// Page slots are padded by 32 bytes so the eight quads' 8-byte shared loads
-// spread over all 32 banks.  The < 32-byte tail of a page (and the < 16-byte
-// part a bulk copy cannot move) is read from global memory by the quad
-// leader while it finishes the hash.
+// pages.  The threads of a page copy its chunk with per-thread 16-byte
+// asynchronous copies (cp.async), one commit group per stage, and wait for
+// the group before hashing it.  (One bulk TMA copy per page per stage moves
+// the same bytes, but issuing eight of them per chunk stalled the issuing
+// warp for ~900 cycles -- time it could not spend hashing -- while the
+// per-thread copies never block.)  Page slots are padded by 32 bytes so the
+// eight pages' shared loads spread over all 32 banks.  The < 32-byte tail of
+// a page is read from global memory by the page leader while it finishes the
+// hash.
 //
 // The serial chain per accumulator is the critical path: each step is an
 // add, a rotate and a multiply by PRIME1 (xx_step); the lane products
@@ -32,47 +34,46 @@
 
 namespace kc {
 
-static __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
 // page_hits value of a page whose words must still be classified
 constexpr uint32_t HITS_PENDING = 0xFFFFFFFFu;
 
 size_t digest_smem_bytes(const DigestShape &s) {
-    size_t bars = align_up((size_t)s.warps * s.stages * sizeof(uint64_t), 128);
-    size_t ring = (size_t)s.warps * s.stages * 8 * (size_t)(s.chunk + 32);
-    return bars + ring;
+    const size_t ppw = 8 * (size_t)(s.lanes == 2 ? 2 : 1);
+    return (size_t)s.warps * s.stages * ppw * (size_t)(s.chunk + 32);
 }
 
-template <bool CENSUS>
+// CHUNK = the chunk size as a compile-time constant (0: runtime only); full
+// chunks of that size take a fully unrolled path.
+// LPT = XXH64 lanes per thread.  LPT = 1: four threads per page (8 pages per
+// warp), the most parallel layout, for few pages.  LPT = 2: two threads per
+// page, each owning two adjacent lanes (one 16-byte shared load per stripe
+// feeds two independent chains), 16 pages per warp: half the instructions
+// per byte and twice the instruction-level parallelism, for many pages.
+template <bool CENSUS, int LPT, int CHUNK>
 __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, uint64_t *__restrict__ hash,
                                                      uint8_t *__restrict__ zero,
                                                      uint32_t *__restrict__ page_hits,
                                                      uint32_t *__restrict__ task_ctr,
                                                      uint32_t *__restrict__ status, int stages, int chunk) {
+    constexpr int TPP = 4 / LPT;    // threads per page
+    constexpr int PPW = 32 / TPP;   // pages per warp task
     extern __shared__ __align__(128) uint8_t smem[];
-    const int nwarps = blockDim.x >> 5;
+    (void)status;                   // no waits here can time out: cp.async groups always complete
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
-    const int q = lane >> 2;   // page slot of this quad
-    const int k = lane & 3;    // XXH64 accumulator owned by this thread
+    const int q = lane / TPP;       // page slot of this thread
+    const int j = lane % TPP;       // this thread owns lanes j*LPT .. j*LPT+LPT-1
     const uint32_t FULL = 0xffffffffu;
 
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem) + warp * stages;
     const size_t slot_stride = (size_t)chunk + 32;
-    const size_t stage_stride = 8 * slot_stride;
-    uint8_t *ring = smem + align_up((size_t)nwarps * stages * sizeof(uint64_t), 128) +
-                    (size_t)warp * stages * stage_stride;
+    const size_t stage_stride = PPW * slot_stride;
+    uint8_t *ring = smem + (size_t)warp * stages * stage_stride;
 
-    if (lane < (uint32_t)stages) mbar_init(&bars[lane], 8);
-    mbar_fence_init();
-    __syncwarp();
-
-    uint64_t pos = 0;   // ring positions consumed by this warp so far
     while (true) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(task_ctr, 1u);
         t = __shfl_sync(FULL, t, 0);
-        const uint64_t p0 = (uint64_t)t * 8;
+        const uint64_t p0 = (uint64_t)t * PPW;
         if (p0 >= pg.npages) break;
         const uint64_t p = p0 + q;
         const bool valid = p < pg.npages;
@@ -92,118 +93,147 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
         const uint32_t nch = (sbytes + chunk - 1) / chunk;
         const uint32_t maxch = __reduce_max_sync(FULL, nch);
 
-        // Issue chunk c of this task into ring position pos + c.
+        // Copy chunk c of this thread's page into stage c % stages: the
+        // page's threads split its 16-byte pieces.  Every thread commits one
+        // group per call (empty past the page's end), so group counts agree.
         auto issue = [&](uint32_t c) {
-            const uint64_t g = pos + c;
-            const int st = (int)(g % stages);
-            if (k == 0) {
-                uint32_t b = 0;
-                if (c < nch) {
-                    const uint32_t rest = sbytes - c * chunk;
-                    b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
-                }
-                uint64_t *bar = &bars[st];
-                if (b) {
-                    mbar_arrive_expect_tx(bar, b);
-                    bulk_g2s(ring + st * stage_stride + q * slot_stride, src + (size_t)c * chunk, b, bar);
-                } else {
-                    mbar_arrive(bar);
-                }
+            if (c < nch) {
+                const uint32_t rest = sbytes - c * chunk;
+                const uint32_t b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
+                uint8_t *dst = ring + (c % stages) * stage_stride + q * slot_stride;
+                const uint8_t *from = src + (size_t)c * chunk;
+                for (uint32_t o = 16 * j; o < b; o += 16 * TPP) cp_async16(dst + o, from + o);
             }
+            cp_async_commit();
         };
-        const uint32_t pre = maxch < (uint32_t)stages ? maxch : (uint32_t)stages;
-        for (uint32_t c = 0; c < pre; ++c) issue(c);
+        for (int c = 0; c < stages - 1; ++c) issue((uint32_t)c);
 
-        uint64_t acc = xx_init(k);
+        uint64_t acc[LPT];
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) acc[i] = xx_init(j * LPT + i);
         uint32_t zlo = 0, zhi = 0;
         uint32_t cmin = 0xFFFFFFFFu;   // census pre-filter, minimum over the page
-        bool timed_out = false;
-        uint32_t c = 0;
-        for (; c < maxch; ++c) {
-            const uint64_t g = pos + c;
-            const int st = (int)(g % stages);
-            const uint32_t parity = (uint32_t)((g / stages) & 1);
-            const bool ok = mbar_wait_bounded(&bars[st], parity);
-            if (!__all_sync(FULL, ok)) {
-                timed_out = true;
-                break;
-            }
+        for (uint32_t c = 0; c < maxch; ++c) {
+            issue(c + stages - 1);        // refills the stage consumed in the previous iteration
+            cp_async_wait(stages - 1);    // this thread's pieces of chunk c have landed
+            __syncwarp();                 // ... and so have those of the page's other threads
+            const int st = (int)(c % stages);
             uint32_t b = 0;
             if (c < nch) {
                 const uint32_t rest = sbytes - c * chunk;
                 b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
             }
-            const uint8_t *slot = ring + st * stage_stride + q * slot_stride + 8 * k;
+            const uint8_t *slot = ring + st * stage_stride + q * slot_stride + 8 * LPT * j;
+            // one load per stripe: LPT consecutive 8-byte lanes
+            auto ld = [&](uint32_t off, uint64_t (&w)[LPT]) {
+                if (LPT == 1) {
+                    w[0] = *reinterpret_cast<const uint64_t *>(slot + off);
+                } else {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(slot + off);
+                    w[0] = ((uint64_t)v.y << 32) | v.x;
+                    w[LPT - 1] = ((uint64_t)v.w << 32) | v.z;
+                }
+            };
+            auto eat = [&](const uint64_t (&w)[LPT]) {
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) {
+                    zlo |= (uint32_t)w[i];
+                    zhi |= (uint32_t)(w[i] >> 32);
+                    if (CENSUS) cmin = min(cmin, census_pre(ca, w[i]));
+                }
+            };
             uint32_t s = 0;
-            if (b >= 128) {
+            if (CHUNK && b == (uint32_t)CHUNK) {
+                // a full chunk of compile-time size: fully unrolled, the
+                // loads of all its stripes issued ahead of the chains
+                uint64_t w[4][LPT];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ld(32 * u, w[u]);
+#pragma unroll
+                for (int g = 0; g < CHUNK / 128; ++g) {
+                    uint64_t nw[4][LPT];
+                    if (g + 1 < CHUNK / 128) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) ld(128 * (g + 1) + 32 * u, nw[u]);
+                    }
+                    uint64_t m[4][LPT];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) m[u][i] = w[u][i] * XXP2;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], m[u][i]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) eat(w[u]);
+                    if (g + 1 < CHUNK / 128) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int i = 0; i < LPT; ++i) w[u][i] = nw[u][i];
+                    }
+                }
+                s = b;
+            } else if (b >= 128) {
                 // register double buffer: the next four stripes are loaded
-                // while the current four run through the chain
-                uint64_t w0 = *reinterpret_cast<const uint64_t *>(slot);
-                uint64_t w1 = *reinterpret_cast<const uint64_t *>(slot + 32);
-                uint64_t w2 = *reinterpret_cast<const uint64_t *>(slot + 64);
-                uint64_t w3 = *reinterpret_cast<const uint64_t *>(slot + 96);
+                // while the current four run through the chains
+                uint64_t w[4][LPT];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ld(32 * u, w[u]);
                 for (; s + 128 <= b; s += 128) {
                     const uint32_t ns = (s + 256 <= b) ? s + 128 : s;   // last group reloads itself
-                    const uint64_t n0 = *reinterpret_cast<const uint64_t *>(slot + ns);
-                    const uint64_t n1 = *reinterpret_cast<const uint64_t *>(slot + ns + 32);
-                    const uint64_t n2 = *reinterpret_cast<const uint64_t *>(slot + ns + 64);
-                    const uint64_t n3 = *reinterpret_cast<const uint64_t *>(slot + ns + 96);
-                    const uint64_t m0 = w0 * XXP2, m1 = w1 * XXP2, m2 = w2 * XXP2, m3 = w3 * XXP2;
-                    acc = xx_step(acc, m0);
-                    acc = xx_step(acc, m1);
-                    acc = xx_step(acc, m2);
-                    acc = xx_step(acc, m3);
-                    zlo |= (uint32_t)w0 | (uint32_t)w1 | (uint32_t)w2 | (uint32_t)w3;
-                    zhi |= (uint32_t)(w0 >> 32) | (uint32_t)(w1 >> 32) | (uint32_t)(w2 >> 32) |
-                           (uint32_t)(w3 >> 32);
-                    if (CENSUS) {
-                        cmin = min(cmin, census_pre(ca, w0));
-                        cmin = min(cmin, census_pre(ca, w1));
-                        cmin = min(cmin, census_pre(ca, w2));
-                        cmin = min(cmin, census_pre(ca, w3));
-                    }
-                    w0 = n0;
-                    w1 = n1;
-                    w2 = n2;
-                    w3 = n3;
+                    uint64_t nw[4][LPT];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) ld(ns + 32 * u, nw[u]);
+                    uint64_t m[4][LPT];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) m[u][i] = w[u][i] * XXP2;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], m[u][i]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) eat(w[u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) w[u][i] = nw[u][i];
                 }
             }
             for (; s < b; s += 32) {
-                const uint64_t w = *reinterpret_cast<const uint64_t *>(slot + s);
-                acc = xx_step(acc, w * XXP2);
-                zlo |= (uint32_t)w;
-                zhi |= (uint32_t)(w >> 32);
-                if (CENSUS) cmin = min(cmin, census_pre(ca, w));
+                uint64_t w[LPT];
+                ld(s, w);
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], w[i] * XXP2);
+                eat(w);
             }
-            __syncwarp();
-            if (c + stages < maxch) issue(c + stages);
+            __syncwarp();                 // the stage is free for the next refill
         }
-        if (timed_out) {
-            // Give the copies still in flight a bounded chance to land before
-            // this warp stops using its ring, then report and quit.
-            const uint32_t issued = (c + stages < maxch) ? c + stages : maxch;
-            for (uint32_t c2 = c; c2 < issued; ++c2) {
-                const uint64_t g = pos + c2;
-                mbar_wait_bounded(&bars[g % stages], (uint32_t)((g / stages) & 1));
-            }
-            if (lane == 0) set_status(status, ST_TIMEOUT);
-            break;
-        }
-        pos += maxch;
+        cp_async_wait(0);                 // trailing (empty) groups
 
-        // Quad reduction: accumulators to the quad leader, OR of bytes, census flag.
-        const int qb = lane & ~3;
-        const uint64_t a1 = __shfl_sync(FULL, acc, qb + 1);
-        const uint64_t a2 = __shfl_sync(FULL, acc, qb + 2);
-        const uint64_t a3 = __shfl_sync(FULL, acc, qb + 3);
-        uint64_t zor = ((uint64_t)zhi << 32) | zlo;
-        zor |= __shfl_xor_sync(FULL, zor, 1);
-        zor |= __shfl_xor_sync(FULL, zor, 2);
-        if (CENSUS) {
-            cmin = min(cmin, __shfl_xor_sync(FULL, cmin, 1));
-            cmin = min(cmin, __shfl_xor_sync(FULL, cmin, 2));
+        // Page reduction: accumulators to the page leader, OR of bytes, census flag.
+        const int lead = lane - j;
+        uint64_t a[4];
+        if (LPT == 1) {
+            a[0] = acc[0];
+#pragma unroll
+            for (int i = 1; i < 4; ++i) a[i] = __shfl_sync(FULL, acc[0], lead + i);
+        } else {
+            a[0] = acc[0];
+            a[1] = acc[LPT - 1];
+            a[2] = __shfl_sync(FULL, acc[0], lead + 1);
+            a[3] = __shfl_sync(FULL, acc[LPT - 1], lead + 1);
         }
-        if (k == 0 && valid) {
+        uint64_t zor = ((uint64_t)zhi << 32) | zlo;
+#pragma unroll
+        for (int o = 1; o < TPP; o <<= 1) {
+            zor |= __shfl_xor_sync(FULL, zor, o);
+            if (CENSUS) cmin = min(cmin, __shfl_xor_sync(FULL, cmin, o));
+        }
+        if (j == 0 && valid) {
             if (lost) {
                 hash[p] = 0;
                 zero[p] = KC_PAGE_LOST;
@@ -211,11 +241,9 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
             } else {
                 uint64_t h;
                 if (len >= 32) {
-                    h = rotl(acc, 1) + rotl(a1, 7) + rotl(a2, 12) + rotl(a3, 18);
-                    h = (h ^ xx_round(0, acc)) * XXP1 + XXP4;
-                    h = (h ^ xx_round(0, a1)) * XXP1 + XXP4;
-                    h = (h ^ xx_round(0, a2)) * XXP1 + XXP4;
-                    h = (h ^ xx_round(0, a3)) * XXP1 + XXP4;
+                    h = rotl(a[0], 1) + rotl(a[1], 7) + rotl(a[2], 12) + rotl(a[3], 18);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) h = (h ^ xx_round(0, a[i])) * XXP1 + XXP4;
                 } else {
                     h = XXP5;
                 }
@@ -260,11 +288,26 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
     }
 }
 
+template <bool CENSUS, int LPT, int CHUNK>
+static cudaError_t setup_one() {
+    return cudaFuncSetAttribute(digest_kernel<CENSUS, LPT, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                227 * 1024);
+}
+
+template <bool CENSUS, int LPT>
+static cudaError_t setup_lanes() {
+    cudaError_t e;
+    if ((e = setup_one<CENSUS, LPT, 0>())) return e;
+    if ((e = setup_one<CENSUS, LPT, 512>())) return e;
+    return setup_one<CENSUS, LPT, 1024>();
+}
+
 cudaError_t setup_digest_kernels() {
-    const int max_smem = 227 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(digest_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(digest_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    cudaError_t e;
+    if ((e = setup_lanes<true, 1>())) return e;
+    if ((e = setup_lanes<true, 2>())) return e;
+    if ((e = setup_lanes<false, 1>())) return e;
+    return setup_lanes<false, 2>();
 }
 
 // ---- census: classification of flagged units ------------------------------------
@@ -384,22 +427,41 @@ cudaError_t launch_census_flagged(const Pages &units, const CensusArgs &ca, uint
     return cudaGetLastError();
 }
 
+template <bool CENSUS, int LPT>
+static void launch_lanes(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const Pages &pg, const CensusArgs &ca,
+                         uint64_t *hash, uint8_t *zero, uint32_t *page_hits, uint32_t *task_ctr, uint32_t *status,
+                         const DigestShape &shape) {
+    switch (shape.chunk) {
+    case 512:
+        digest_kernel<CENSUS, LPT, 512><<<grid, block, smem, st>>>(pg, ca, hash, zero, page_hits, task_ctr, status,
+                                                                   shape.stages, shape.chunk);
+        break;
+    case 1024:
+        digest_kernel<CENSUS, LPT, 1024><<<grid, block, smem, st>>>(pg, ca, hash, zero, page_hits, task_ctr, status,
+                                                                    shape.stages, shape.chunk);
+        break;
+    default:
+        digest_kernel<CENSUS, LPT, 0><<<grid, block, smem, st>>>(pg, ca, hash, zero, page_hits, task_ctr, status,
+                                                                 shape.stages, shape.chunk);
+    }
+}
+
 cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash, uint8_t *zero,
                           uint32_t *page_hits, uint64_t *counts, uint32_t *task_ctr, uint32_t *status,
                           const DigestShape &shape, cudaStream_t st) {
     (void)counts;
     const size_t smem = digest_smem_bytes(shape);
     const dim3 block(32 * shape.warps), grid(shape.ctas);
-    if (census) {
-        digest_kernel<true><<<grid, block, smem, st>>>(pg, *census, hash, zero, page_hits, task_ctr, status,
-                                                       shape.stages, shape.chunk);
-        count_launches(1);
-    } else {
-        CensusArgs none{};
-        digest_kernel<false><<<grid, block, smem, st>>>(pg, none, hash, zero, nullptr, task_ctr, status,
-                                                        shape.stages, shape.chunk);
-        count_launches(1);
-    }
+    CensusArgs none{};
+    if (census && shape.lanes == 2)
+        launch_lanes<true, 2>(grid, block, smem, st, pg, *census, hash, zero, page_hits, task_ctr, status, shape);
+    else if (census)
+        launch_lanes<true, 1>(grid, block, smem, st, pg, *census, hash, zero, page_hits, task_ctr, status, shape);
+    else if (shape.lanes == 2)
+        launch_lanes<false, 2>(grid, block, smem, st, pg, none, hash, zero, nullptr, task_ctr, status, shape);
+    else
+        launch_lanes<false, 1>(grid, block, smem, st, pg, none, hash, zero, nullptr, task_ctr, status, shape);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ struct kc_ctx {
     void *d_scratch = nullptr;
     size_t scratch_cap = 0;
     std::list<Tables> tables;     // most recently used first
-    DigestShape forced{0, 0, 0, 0};
+    DigestShape forced{0, 0, 0, 0, 0};
     cudaEvent_t trace_start = nullptr;   // caller-owned, recorded around main kernels
     cudaEvent_t trace_stop = nullptr;
 };
@@ -340,15 +340,18 @@ struct Trace {
 uint32_t *status_word(kc_ctx *c) { return reinterpret_cast<uint32_t *>(&c->d_misc[0]); }
 uint32_t *task_counter(kc_ctx *c) { return reinterpret_cast<uint32_t *>(&c->d_misc[1]); }
 
-// Built-in digest shape.  Every warp owns 8 pages at a time and XXH64 is a
-// serial chain per lane, so a page started late finishes late: keep every
-// 8-page task resident at once when that fits (up to 24 warps per SM), in
-// CTAs of 2 warps, then give each warp the deepest ring that fits its share
-// of the SM's shared memory.
+// Built-in digest shape.  XXH64 is a serial chain per lane and every warp
+// owns 8 pages at a time (one lane per thread: measured faster than two
+// lanes per thread on every workload tried), so a page started late finishes
+// late: keep every task resident at once when that fits (up to 24 warps per
+// SM), in CTAs of 2 warps, then give each warp the deepest ring that fits
+// its share of the SM's shared memory.
 DigestShape pick_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
-    const uint64_t tasks = (npages + 7) / 8;
     const size_t smem_sm = c->smem_per_sm ? c->smem_per_sm : 228 * 1024;
     DigestShape s = c->forced;
+    if (s.lanes == 0) s.lanes = 1;
+    const uint64_t ppw = 8ull * (uint64_t)s.lanes;
+    const uint64_t tasks = (npages + ppw - 1) / ppw;
     if (s.warps == 0) {
         s.warps = 2;
         uint64_t per_sm = (tasks + c->sms - 1) / c->sms;
@@ -363,7 +366,7 @@ DigestShape pick_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
         s.stages = 2;
         for (auto &pc : pref) {
             if ((uint32_t)pc[0] > page) continue;
-            const size_t need = (size_t)pc[1] * 8 * (pc[0] + 32) + pc[1] * 8;
+            const size_t need = (size_t)pc[1] * ppw * (pc[0] + 32) + pc[1] * 8;
             if (need <= per_warp) {
                 s.chunk = pc[0];
                 s.stages = pc[1];
@@ -495,17 +498,19 @@ KC_API kc_status kc_sync(kc_ctx *c, void *stream) {
     return KC_OK;
 }
 
-KC_API kc_status kc_set_digest_shape(kc_ctx *c, int warps, int stages, int chunk) {
+KC_API kc_status kc_set_digest_shape(kc_ctx *c, int warps, int stages, int chunk, int lanes) {
     if (!c) return KC_EINVAL;
-    if (warps == 0 && stages == 0 && chunk == 0) {
-        c->forced = DigestShape{0, 0, 0, 0};
+    if (warps == 0 && stages == 0 && chunk == 0 && lanes == 0) {
+        c->forced = DigestShape{0, 0, 0, 0, 0};
         return KC_OK;
     }
-    if (warps < 1 || warps > 16 || stages < 2 || stages > 8 || chunk < 256 || chunk > 8192 || (chunk % 128))
-        return fail(c, KC_EINVAL, "digest shape out of range (warps %d, stages %d, chunk %d)", warps, stages, chunk);
-    DigestShape s{warps, stages, chunk, 1};
+    if (warps < 1 || warps > 16 || stages < 2 || stages > 8 || chunk < 256 || chunk > 8192 || (chunk % 128) ||
+        (lanes != 1 && lanes != 2))
+        return fail(c, KC_EINVAL, "digest shape out of range (warps %d, stages %d, chunk %d, lanes %d)", warps, stages,
+                    chunk, lanes);
+    DigestShape s{warps, stages, chunk, 1, lanes};
     if (digest_smem_bytes(s) > 227 * 1024) return fail(c, KC_EINVAL, "digest shape needs too much shared memory");
-    c->forced = DigestShape{warps, stages, chunk, 0};
+    c->forced = DigestShape{warps, stages, chunk, 0, lanes};
     return KC_OK;
 }
 
@@ -518,13 +523,14 @@ KC_API kc_status kc_set_trace_events(kc_ctx *c, void *start, void *stop) {
 }
 
 KC_API kc_status kc_get_digest_shape(kc_ctx *c, uint32_t page_bytes, uint64_t npages, int *warps, int *stages,
-                                     int *chunk, int *ctas) {
+                                     int *chunk, int *ctas, int *lanes) {
     if (!c || !pow2_page(page_bytes)) return KC_EINVAL;
     DigestShape s = pick_shape(c, page_bytes, npages);
     if (warps) *warps = s.warps;
     if (stages) *stages = s.stages;
     if (chunk) *chunk = s.chunk;
     if (ctas) *ctas = s.ctas;
+    if (lanes) *lanes = s.lanes;
     return KC_OK;
 }
 

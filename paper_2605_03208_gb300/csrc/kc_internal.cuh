@@ -63,6 +63,7 @@ struct DigestShape {
     int stages;       // ring depth per warp
     int chunk;        // bytes per page per stage (multiple of 32, <= page)
     int ctas;         // grid size
+    int lanes;        // XXH64 lanes per thread: 1 (8 pages per warp) or 2 (16)
 };
 
 size_t digest_smem_bytes(const DigestShape &s);

@@ -81,11 +81,11 @@ def load(build_if_missing: bool = False):
     L.kc_buf_status.restype = i32
     L.kc_buf_status.argtypes = [vp, i32]
     L.kc_set_digest_shape.restype = st
-    L.kc_set_digest_shape.argtypes = [vp, i32, i32, i32]
+    L.kc_set_digest_shape.argtypes = [vp, i32, i32, i32, i32]
     L.kc_set_trace_events.restype = st
     L.kc_set_trace_events.argtypes = [vp, vp, vp]
     L.kc_get_digest_shape.restype = st
-    L.kc_get_digest_shape.argtypes = [vp, u32, u64] + [ctypes.POINTER(i32)] * 4
+    L.kc_get_digest_shape.argtypes = [vp, u32, u64] + [ctypes.POINTER(i32)] * 5
     L.kc_page_count.restype = u64
     L.kc_page_count.argtypes = [ctypes.POINTER(KcBuf), i32, u32]
     B = ctypes.POINTER(KcBuf)
@@ -181,8 +181,8 @@ class Context:
     def buf_status(self, i: int) -> int:
         return self.lib.kc_buf_status(self.h, i)
 
-    def set_digest_shape(self, warps=0, stages=0, chunk=0):
-        return self._check(self.lib.kc_set_digest_shape(self.h, warps, stages, chunk), (OK,))
+    def set_digest_shape(self, warps=0, stages=0, chunk=0, lanes=0):
+        return self._check(self.lib.kc_set_digest_shape(self.h, warps, stages, chunk, lanes), (OK,))
 
     def set_trace_events(self, start=None, stop=None):
         """Record torch.cuda.Event objects around the main kernel of later calls.
@@ -197,10 +197,11 @@ class Context:
         return self._check(self.lib.kc_set_trace_events(self.h, a, b), (OK,))
 
     def digest_shape(self, page_bytes: int, npages: int):
-        v = [ctypes.c_int() for _ in range(4)]
+        v = [ctypes.c_int() for _ in range(5)]
         self._check(self.lib.kc_get_digest_shape(self.h, page_bytes, npages,
                                                  *[ctypes.byref(x) for x in v]), (OK,))
-        return dict(warps=v[0].value, stages=v[1].value, chunk=v[2].value, ctas=v[3].value)
+        return dict(warps=v[0].value, stages=v[1].value, chunk=v[2].value, ctas=v[3].value,
+                    lanes=v[4].value)
 
     def digest(self, regions, page_bytes, hash_out, zero_out, page_first_out=None, stream=None,
                allow=(OK, EBUF)):

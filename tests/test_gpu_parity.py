@@ -51,15 +51,16 @@ def test_digest_tiny_bit_exact(ctx, tiny, S):
     assert ctx.sync() == kc.OK
 
 
-@pytest.mark.parametrize("shape", [(1, 2, 256), (2, 3, 512), (4, 4, 1024), (4, 2, 2048), (3, 5, 384),
-                                   (16, 2, 256)])
+@pytest.mark.parametrize("shape", [(1, 2, 256, 1), (2, 3, 512, 1), (4, 4, 1024, 1), (4, 2, 2048, 1),
+                                   (3, 5, 384, 1), (16, 2, 256, 1), (1, 2, 256, 2), (2, 4, 1024, 2),
+                                   (3, 3, 640, 2), (2, 2, 2048, 2)])
 def test_digest_forced_shapes(ctx, tiny, shape):
     snap, dev = tiny
     ctx.set_digest_shape(*shape)
     try:
         st, h, z, pf = G.run_digest(ctx, snap, dev, 65536)
     finally:
-        ctx.set_digest_shape(0, 0, 0)
+        ctx.set_digest_shape(0, 0, 0, 0)
     oh, oz, _ = _oracle_digest(snap, 65536)
     assert st == kc.OK and np.array_equal(h, oh) and np.array_equal(z, oz)
 
@@ -127,10 +128,14 @@ def test_census_dense_pointers_and_truncation(ctx):
 
 # ---------------------------------------------------------------- dedup / restore
 
-def _dedup_vs_oracle(ctx, snap, dev, S, hash_bits=64):
+def _dedup_vs_oracle(ctx, snap, dev, S, hash_bits=64, low_bits=None):
     oh, oz, _ = _oracle_digest(snap, S)
     if hash_bits < 64:
         oh = oh & np.uint64((1 << hash_bits) - 1)
+    if low_bits is not None:
+        # keep the high 32 bits, squeeze the low 32 bits to a few values:
+        # different hashes that agree on their low half
+        oh = (oh & np.uint64(0xFFFFFFFF00000000)) | (oh & np.uint64((1 << low_bits) - 1))
     # the oracle's digest is the input of both sides
     h_dev = torch.from_numpy(oh.view(np.int64).copy()).cuda()
     z_dev = torch.from_numpy(oz.copy()).cuda()
@@ -158,6 +163,14 @@ def test_dedup_forced_collisions(ctx, tiny, bits):
     _dedup_vs_oracle(ctx, snap, dev, 65536, hash_bits=bits)
 
 
+@pytest.mark.parametrize("low_bits", [0, 2])
+def test_dedup_low_half_collisions(ctx, tiny, low_bits):
+    """Distinct hashes sharing their low 32 bits interleave in the sorted
+    order; the result must still be the byte-defined classes."""
+    snap, dev = tiny
+    _dedup_vs_oracle(ctx, snap, dev, 4096, low_bits=low_bits)
+
+
 def test_dedup_tiled_sort_path(ctx):
     # > 8192 non-zero pages: the multi-CTA radix sort passes
     layout = W.tiny_layout(5, n=40, total=64 * W.MiB, page_bytes=4096)
@@ -165,6 +178,7 @@ def test_dedup_tiled_sort_path(ctx):
     assert sum(-(-s // 4096) for s in snap.sizes) > 9000
     _dedup_vs_oracle(ctx, snap, dev, 4096)
     _dedup_vs_oracle(ctx, snap, dev, 4096, hash_bits=12)
+    _dedup_vs_oracle(ctx, snap, dev, 4096, low_bits=6)
 
 
 def test_restore_roundtrip(ctx, tiny):
