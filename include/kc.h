@@ -292,6 +292,64 @@ KC_API kc_status kc_restore(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t p
 KC_API kc_status kc_compare(kc_ctx *ctx, const kc_buf *got, const kc_buf *want, int npairs,
                      double atol, double rtol, kc_cmp_result *d_out, void *stream);
 
+/* ---- batched form --------------------------------------------------------
+ * The operations above launch a few kernels per call; validating thousands
+ * of replayed buffers (one tuning campaign re-runs a kernel many times and
+ * compares every output region) that way spends most of its time in
+ * launches.  kc_batch_run digests and/or compares many buffers in one
+ * persistent, work-stealing launch.  (The paper has no batched form; its
+ * validator compares regions one after another on the host -- Section
+ * "Replay Validation".)
+ *
+ * A job is one buffer: with KC_JOB_DIGEST its pages are hashed exactly as
+ * kc_digest would (into its own d_hash / d_zero, ceil(bytes / page_bytes)
+ * entries each); with KC_JOB_COMPARE it is compared with want_va exactly as
+ * kc_compare would (into d_cmp).  KC_BUF_LOST marks a buffer that could not
+ * be read (outputs marked as by the single-operation calls).
+ *
+ * work / nwork: which units this launch processes, as ranges of a job's
+ * pages (KC_WORK_DIGEST) or of its comparison items (KC_WORK_COMPARE,
+ * KC_BATCH_ITEM_BYTES of each buffer per item).  NULL = every unit of every
+ * job, largest jobs first.  A job may be spread over several launches (a
+ * serving loop does this); its comparison record is initialised by the
+ * launch whose job carries KC_JOB_INIT and accumulates over later launches
+ * with order-independent merges, so the result does not depend on how the
+ * work was split.  Without `work`, every compare job is initialised.
+ *
+ * Repeated calls with the same jobs and work hit the context's table cache
+ * and can be captured in a CUDA graph.  The digest kernel shape
+ * (kc_set_digest_shape) also applies here.
+ * Errors: KC_EINVAL (alignment, sizes, dtype, null outputs, a work range
+ * outside its job), KC_EBUF (a lost buffer; the others are complete). */
+#define KC_JOB_DIGEST 0x10
+#define KC_JOB_COMPARE 0x20
+#define KC_JOB_INIT 0x40
+#define KC_WORK_DIGEST 0
+#define KC_WORK_COMPARE 1
+#define KC_BATCH_ITEM_BYTES 65536
+
+typedef struct {
+    uint64_t got_va;       /* buffer to digest and/or compare (16-byte aligned) */
+    uint64_t want_va;      /* comparison reference (KC_JOB_COMPARE), same size */
+    uint64_t bytes;        /* size of the buffer(s) */
+    int32_t dtype;         /* element type for the comparison */
+    int32_t flags;         /* KC_JOB_* | KC_BUF_LOST */
+    uint64_t *d_hash;      /* KC_JOB_DIGEST: page hashes */
+    uint8_t *d_zero;       /* KC_JOB_DIGEST: page zero flags */
+    kc_cmp_result *d_cmp;  /* KC_JOB_COMPARE: the comparison record */
+    uint64_t reserved;
+} kc_job;
+
+typedef struct {
+    uint32_t job;          /* index in the job list */
+    uint32_t kind;         /* KC_WORK_DIGEST or KC_WORK_COMPARE */
+    uint64_t first;        /* first unit (page, or comparison item) */
+    uint64_t count;        /* number of units */
+} kc_work;
+
+KC_API kc_status kc_batch_run(kc_ctx *ctx, const kc_job *jobs, int njobs, uint32_t page_bytes, double atol,
+                              double rtol, const kc_work *work, int nwork, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

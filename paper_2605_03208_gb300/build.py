@@ -18,12 +18,12 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["kc_api.cu", "k_digest.cu", "k_dedup.cu", "k_restore.cu", "k_compare.cu", "kc_noalloc.cu"]
+SOURCES = ["kc_api.cu", "k_digest.cu", "k_dedup.cu", "k_restore.cu", "k_compare.cu", "k_batch.cu", "kc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
                  "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE]
 # FP64 error values must be single IEEE operations: no multiply-add contraction.
-EXTRA = {"k_compare.cu": ["-fmad=false"]}
+EXTRA = {"k_compare.cu": ["-fmad=false"], "k_batch.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:

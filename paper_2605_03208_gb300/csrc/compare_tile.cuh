@@ -1,0 +1,236 @@
+// compare_tile.cuh -- per-element comparison of a tile of a (got, want)
+// pair, shared by the comparison kernel and the batched kernel (Section
+// "Replay Validation": numpy.allclose-style tolerance comparison with NaNs
+// reported explicitly).
+//
+// Each thread streams 16-byte vectors of both buffers.  A vector whose 16
+// bytes are bitwise equal in got and want only needs its NaNs counted (equal
+// bits are equal values, NaN == NaN), so the FP64 unit -- slow on this part
+// -- is used only for elements whose bits differ: those are widened exactly
+// to double, and the error values are one IEEE operation each (__dsub_rn,
+// __ddiv_rn, __dmul_rn, __dadd_rn: no FMA contraction), hence identical to
+// any other correctly rounded evaluation.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <math_constants.h>
+
+#include "kc_device.cuh"
+
+namespace kc {
+
+struct CmpAcc {
+    unsigned long long mism, first, nan_g, nan_w, nan_m;
+    double max_abs, max_rel;
+};
+
+template <int DT>
+__device__ __forceinline__ double widen(uint32_t bits) {
+    if (DT == KC_F32) return (double)__uint_as_float(bits);
+    if (DT == KC_BF16) return (double)__uint_as_float(bits << 16);
+    if (DT == KC_F16) return (double)__half2float(__ushort_as_half((unsigned short)bits));
+    if (DT == KC_I32) return (double)(int32_t)bits;
+    return (double)bits;   // KC_U8 / KC_RAW
+}
+
+// NaN test on the raw bits of one element.
+template <int DT>
+__device__ __forceinline__ bool bits_nan(uint32_t bits) {
+    if (DT == KC_F32) return (bits & 0x7fffffffu) > 0x7f800000u;
+    if (DT == KC_BF16) return (bits & 0x7fffu) > 0x7f80u;
+    if (DT == KC_F16) return (bits & 0x7fffu) > 0x7c00u;
+    return false;
+}
+
+template <int DT>
+__device__ __forceinline__ void cmp_slow(uint32_t gb, uint32_t wb, unsigned long long idx, double atol,
+                                         double rtol, CmpAcc &acc) {
+    const double a = widen<DT>(gb), b = widen<DT>(wb);
+    const bool na = isnan(a), nb = isnan(b);
+    acc.nan_g += na;
+    acc.nan_w += nb;
+    if (na && nb) return;
+    if (na != nb) {
+        acc.mism += 1;
+        acc.nan_m += 1;
+        acc.first = idx < acc.first ? idx : acc.first;
+        return;
+    }
+    if (a == b) return;
+    const double d = fabs(__dsub_rn(a, b));
+    const double r = (b == 0.0 || isinf(d)) ? CUDART_INF : __ddiv_rn(d, fabs(b));
+    acc.max_abs = d > acc.max_abs ? d : acc.max_abs;
+    acc.max_rel = r > acc.max_rel ? r : acc.max_rel;
+    const bool mis = isinf(a) || isinf(b) || d > __dadd_rn(atol, __dmul_rn(rtol, fabs(b)));
+    if (mis) {
+        acc.mism += 1;
+        acc.first = idx < acc.first ? idx : acc.first;
+    }
+}
+
+template <int DT>
+__host__ __device__ constexpr int esize() {
+    return DT == KC_F32 || DT == KC_I32 ? 4 : DT == KC_F16 || DT == KC_BF16 ? 2 : 1;
+}
+
+// Element j (0-based) of a 32-bit word.
+template <int DT>
+__device__ __forceinline__ uint32_t elem_of(uint32_t w, int j) {
+    if (esize<DT>() == 4) return w;
+    if (esize<DT>() == 2) return (w >> (16 * j)) & 0xffffu;
+    return (w >> (8 * j)) & 0xffu;
+}
+
+// NaNs in a word whose got and want bits are identical.
+template <int DT>
+__device__ __forceinline__ uint32_t word_nans(uint32_t w) {
+    if (DT == KC_F32) return bits_nan<DT>(w);
+    if (DT == KC_BF16 || DT == KC_F16) return bits_nan<DT>(w & 0xffffu) + bits_nan<DT>(w >> 16);
+    return 0;
+}
+
+template <int DT>
+__device__ __forceinline__ void cmp_word(uint32_t g, uint32_t w, unsigned long long first_elem,
+                                         double atol, double rtol, CmpAcc &acc) {
+    constexpr int per = 4 / esize<DT>();
+    if (g == w) {
+        const uint32_t n = word_nans<DT>(g);
+        acc.nan_g += n;
+        acc.nan_w += n;
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+        const uint32_t ge = elem_of<DT>(g, j), we = elem_of<DT>(w, j);
+        if (ge == we) {
+            const uint32_t n = bits_nan<DT>(ge);
+            acc.nan_g += n;
+            acc.nan_w += n;
+        } else {
+            cmp_slow<DT>(ge, we, first_elem + j, atol, rtol, acc);
+        }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void cmp_vec(uint4 g, uint4 w, unsigned long long first_elem, double atol,
+                                        double rtol, CmpAcc &acc) {
+    constexpr int per = 4 / esize<DT>();
+    if (g.x == w.x && g.y == w.y && g.z == w.z && g.w == w.w) {
+        if (DT == KC_F32 || DT == KC_F16 || DT == KC_BF16) {
+            const uint32_t n = word_nans<DT>(g.x) + word_nans<DT>(g.y) + word_nans<DT>(g.z) +
+                               word_nans<DT>(g.w);
+            acc.nan_g += n;
+            acc.nan_w += n;
+        }
+        return;
+    }
+    cmp_word<DT>(g.x, w.x, first_elem, atol, rtol, acc);
+    cmp_word<DT>(g.y, w.y, first_elem + per, atol, rtol, acc);
+    cmp_word<DT>(g.z, w.z, first_elem + 2 * per, atol, rtol, acc);
+    cmp_word<DT>(g.w, w.w, first_elem + 3 * per, atol, rtol, acc);
+}
+
+// One tile of one pair, shared by `nthr` threads (tid = 0 .. nthr-1).
+template <int DT>
+__device__ void cmp_tile(const CmpPair &pr, uint64_t tile_in_pair, double atol, double rtol, CmpAcc &acc,
+                         uint32_t tid, uint32_t nthr) {
+    constexpr int ES = esize<DT>();
+    const uint64_t nbytes = pr.nelem * ES;
+    const uint64_t t0 = tile_in_pair * CMP_TILE_BYTES;
+    const uint64_t tlen = nbytes - t0 < CMP_TILE_BYTES ? nbytes - t0 : CMP_TILE_BYTES;
+    const uint8_t *g = reinterpret_cast<const uint8_t *>(pr.got) + t0;
+    const uint8_t *w = reinterpret_cast<const uint8_t *>(pr.want) + t0;
+    const uint64_t nvec = tlen >> 4;
+    uint64_t v = tid;
+    for (; v + 3 * nthr < nvec; v += 4 * nthr) {
+        uint4 gv[4], wv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            gv[j] = ldg_stream(g + 16 * (v + j * nthr));
+            wv[j] = ldg_stream(w + 16 * (v + j * nthr));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            cmp_vec<DT>(gv[j], wv[j], (t0 + 16 * (v + j * nthr)) / ES, atol, rtol, acc);
+    }
+    for (; v < nvec; v += nthr) {
+        uint4 gv = ldg_stream(g + 16 * v), wv = ldg_stream(w + 16 * v);
+        cmp_vec<DT>(gv, wv, (t0 + 16 * v) / ES, atol, rtol, acc);
+    }
+    // ragged end of the pair: fewer than 16 bytes, element by element
+    const uint64_t tail0 = nvec << 4;
+    for (uint64_t b = tail0 + (uint64_t)tid * ES; b < tlen; b += (uint64_t)nthr * ES) {
+        uint32_t gb = 0, wb = 0;
+        for (int j = 0; j < ES; ++j) {
+            gb |= (uint32_t)g[b + j] << (8 * j);
+            wb |= (uint32_t)w[b + j] << (8 * j);
+        }
+        if (gb == wb) {
+            const uint32_t n = bits_nan<DT>(gb);
+            acc.nan_g += n;
+            acc.nan_w += n;
+        } else {
+            cmp_slow<DT>(gb, wb, (t0 + b) / ES, atol, rtol, acc);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// Reduce a warp's accumulators and merge them into the pair's record with
+// order-independent atomics (lane 0).
+__device__ __forceinline__ void cmp_warp_flush(const CmpAcc &acc, kc_cmp_result *o) {
+    unsigned long long v[7] = {acc.mism, acc.first, acc.nan_g, acc.nan_w, acc.nan_m, dbits(acc.max_abs),
+                               dbits(acc.max_rel)};
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+        const unsigned long long f = __shfl_xor_sync(0xffffffffu, v[1], off);
+        v[1] = f < v[1] ? f : v[1];
+        v[2] += __shfl_xor_sync(0xffffffffu, v[2], off);
+        v[3] += __shfl_xor_sync(0xffffffffu, v[3], off);
+        v[4] += __shfl_xor_sync(0xffffffffu, v[4], off);
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, v[5], off);
+        v[5] = a > v[5] ? a : v[5];
+        const unsigned long long r = __shfl_xor_sync(0xffffffffu, v[6], off);
+        v[6] = r > v[6] ? r : v[6];
+    }
+    if (lane_id() == 0) {
+        if (v[0]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->mismatches), v[0]);
+        if (v[1] != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(&o->first), v[1]);
+        if (v[2]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_got), v[2]);
+        if (v[3]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_want), v[3]);
+        if (v[4]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->nan_mismatch), v[4]);
+        if (v[5]) atomicMax(reinterpret_cast<unsigned long long *>(&o->max_abs), v[5]);
+        if (v[6]) atomicMax(reinterpret_cast<unsigned long long *>(&o->max_rel), v[6]);
+    }
+}
+
+// Comparison of one tile by `nthr` threads, dispatched on the pair's dtype.
+__device__ __forceinline__ void cmp_tile_any(const CmpPair &pr, uint64_t tile, double atol, double rtol, CmpAcc &acc,
+                                             uint32_t tid, uint32_t nthr) {
+    switch (pr.dtype) {
+    case KC_F32: cmp_tile<KC_F32>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_F16: cmp_tile<KC_F16>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_BF16: cmp_tile<KC_BF16>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_I32: cmp_tile<KC_I32>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    default: cmp_tile<KC_U8>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    }
+}
+
+__device__ __forceinline__ void cmp_record_init(kc_cmp_result *o, int32_t status) {
+    kc_cmp_result r;
+    r.mismatches = 0;
+    r.first = -1;
+    r.max_abs = 0.0;
+    r.max_rel = 0.0;
+    r.nan_got = 0;
+    r.nan_want = 0;
+    r.nan_mismatch = 0;
+    r.status = status;
+    r.reserved = 0;
+    *o = r;
+}
+
+}  // namespace kc

@@ -1,0 +1,241 @@
+// digest_task.cuh -- one warp hashes one task of pages: XXH64 (seed 0) of
+// each page, its zero flag and (optionally) its census pre-filter flag.
+// Shared by the digest kernel and the batched persistent kernel.
+//
+// XXH64 keeps four serial accumulators, one per 8-byte lane of every 32-byte
+// stripe.  With LPT lanes per thread, a page is hashed by TPP = 4 / LPT
+// threads and a warp holds PPW = 32 / TPP pages.  The warp owns a ring of
+// `stages` shared-memory stages; a stage holds one `chunk` of each of its
+// pages.  The threads of a page copy its chunk with per-thread 16-byte
+// asynchronous copies (cp.async), one commit group per stage, and wait for
+// the group before hashing it.  (One bulk TMA copy per page per stage moves
+// the same bytes, but issuing eight of them per chunk stalled the issuing
+// warp for ~900 cycles -- time it could not spend hashing -- while the
+// per-thread copies never block.)  Page slots are padded by 32 bytes so the
+// pages' shared loads spread over all 32 banks.  The < 32-byte tail of a
+// page is read from global memory by the page leader while it finishes.
+//
+// The serial chain per accumulator is the critical path: each step is an
+// add, a rotate and a multiply by PRIME1 (xx_step); the lane products
+// (lane * PRIME2) and the next stripes' shared loads are issued ahead of it.
+// CHUNK (compile-time, 0 = none) gives full chunks of that size a fully
+// unrolled path.
+//
+// Census pre-filter: the hashing loop keeps, per page, the minimum of
+// (high 32 bits of a word - pre_lo), a branch-free conservative test of
+// whether any word can be a census hit.
+#pragma once
+
+#include "kc_device.cuh"
+
+namespace kc {
+
+struct PageDigest {
+    uint64_t hash;
+    bool zero;   // every byte is 0
+    bool cand;   // some word passed the census pre-filter
+};
+
+// All 32 lanes of the warp call this together.  Each thread passes its
+// page: src/len (len 0 for a slot without a page) and lost (not readable:
+// no bytes are touched).  The result is valid in the page leader (the
+// thread whose lane % TPP == 0).
+template <bool CENSUS, int LPT, int CHUNK>
+__device__ __forceinline__ PageDigest digest_pages(uint8_t *ring, int stages, int chunk, const uint8_t *src,
+                                                   uint64_t len, bool lost, const CensusArgs &ca) {
+    constexpr int TPP = 4 / LPT;    // threads per page
+    constexpr int PPW = 32 / TPP;   // pages per warp
+    const uint32_t FULL = 0xffffffffu;
+    const uint32_t lane = lane_id();
+    const int q = lane / TPP;       // page slot of this thread
+    const int j = lane % TPP;       // this thread owns lanes j*LPT .. j*LPT+LPT-1
+    const size_t slot_stride = (size_t)chunk + 32;
+    const size_t stage_stride = PPW * slot_stride;
+
+    const uint32_t sbytes = lost ? 0u : (uint32_t)(len & ~31ull);   // bytes in full stripes
+    const uint32_t nch = (sbytes + chunk - 1) / chunk;
+    const uint32_t maxch = __reduce_max_sync(FULL, nch);
+
+    // Copy chunk c of this thread's page into stage c % stages: the page's
+    // threads split its 16-byte pieces.  Every thread commits one group per
+    // call (empty past the page's end), so group counts agree.
+    auto issue = [&](uint32_t c) {
+        if (c < nch) {
+            const uint32_t rest = sbytes - c * chunk;
+            const uint32_t b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
+            uint8_t *dst = ring + (c % stages) * stage_stride + q * slot_stride;
+            const uint8_t *from = src + (size_t)c * chunk;
+            for (uint32_t o = 16 * j; o < b; o += 16 * TPP) cp_async16(dst + o, from + o);
+        }
+        cp_async_commit();
+    };
+    for (int c = 0; c < stages - 1; ++c) issue((uint32_t)c);
+
+    uint64_t acc[LPT];
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) acc[i] = xx_init(j * LPT + i);
+    uint32_t zlo = 0, zhi = 0;
+    uint32_t cmin = 0xFFFFFFFFu;
+    for (uint32_t c = 0; c < maxch; ++c) {
+        issue(c + stages - 1);        // refills the stage consumed in the previous iteration
+        cp_async_wait(stages - 1);    // this thread's pieces of chunk c have landed
+        __syncwarp();                 // ... and so have those of the page's other threads
+        const int st = (int)(c % stages);
+        uint32_t b = 0;
+        if (c < nch) {
+            const uint32_t rest = sbytes - c * chunk;
+            b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
+        }
+        const uint8_t *slot = ring + st * stage_stride + q * slot_stride + 8 * LPT * j;
+        // one load per stripe: LPT consecutive 8-byte lanes
+        auto ld = [&](uint32_t off, uint64_t (&w)[LPT]) {
+            if (LPT == 1) {
+                w[0] = *reinterpret_cast<const uint64_t *>(slot + off);
+            } else {
+                const uint4 v = *reinterpret_cast<const uint4 *>(slot + off);
+                w[0] = ((uint64_t)v.y << 32) | v.x;
+                w[LPT - 1] = ((uint64_t)v.w << 32) | v.z;
+            }
+        };
+        auto eat = [&](const uint64_t (&w)[LPT]) {
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) {
+                zlo |= (uint32_t)w[i];
+                zhi |= (uint32_t)(w[i] >> 32);
+                if (CENSUS) cmin = min(cmin, census_pre(ca, w[i]));
+            }
+        };
+        auto group = [&](const uint64_t (&w)[4][LPT]) {
+            uint64_t m[4][LPT];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) m[u][i] = w[u][i] * XXP2;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], m[u][i]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) eat(w[u]);
+        };
+        uint32_t s = 0;
+        if (CHUNK && b == (uint32_t)CHUNK) {
+            // a full chunk of compile-time size: fully unrolled, the loads of
+            // the next four stripes issued ahead of the chains
+            uint64_t w[4][LPT];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ld(32 * u, w[u]);
+#pragma unroll
+            for (int g = 0; g < (CHUNK ? CHUNK : 128) / 128; ++g) {
+                uint64_t nw[4][LPT];
+                if (g + 1 < CHUNK / 128) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) ld(128 * (g + 1) + 32 * u, nw[u]);
+                }
+                group(w);
+                if (g + 1 < CHUNK / 128) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int i = 0; i < LPT; ++i) w[u][i] = nw[u][i];
+                }
+            }
+            s = b;
+        } else if (b >= 128) {
+            // register double buffer: the next four stripes are loaded while
+            // the current four run through the chains
+            uint64_t w[4][LPT];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ld(32 * u, w[u]);
+            for (; s + 128 <= b; s += 128) {
+                const uint32_t ns = (s + 256 <= b) ? s + 128 : s;   // last group reloads itself
+                uint64_t nw[4][LPT];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ld(ns + 32 * u, nw[u]);
+                group(w);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int i = 0; i < LPT; ++i) w[u][i] = nw[u][i];
+            }
+        }
+        for (; s < b; s += 32) {
+            uint64_t w[LPT];
+            ld(s, w);
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], w[i] * XXP2);
+            eat(w);
+        }
+        __syncwarp();                 // the stage is free for the next refill
+    }
+    cp_async_wait(0);                 // trailing (empty) groups
+
+    // Page reduction: accumulators to the page leader, OR of bytes, census flag.
+    const int lead = lane - j;
+    uint64_t a[4];
+    if (LPT == 1) {
+        a[0] = acc[0];
+#pragma unroll
+        for (int i = 1; i < 4; ++i) a[i] = __shfl_sync(FULL, acc[0], lead + i);
+    } else {
+        a[0] = acc[0];
+        a[1] = acc[LPT - 1];
+        a[2] = __shfl_sync(FULL, acc[0], lead + 1);
+        a[3] = __shfl_sync(FULL, acc[LPT - 1], lead + 1);
+    }
+    uint64_t zor = ((uint64_t)zhi << 32) | zlo;
+#pragma unroll
+    for (int o = 1; o < TPP; o <<= 1) {
+        zor |= __shfl_xor_sync(FULL, zor, o);
+        if (CENSUS) cmin = min(cmin, __shfl_xor_sync(FULL, cmin, o));
+    }
+    PageDigest r{0, false, false};
+    if (j != 0 || lost) return r;
+    uint64_t h;
+    if (len >= 32) {
+        h = rotl(a[0], 1) + rotl(a[1], 7) + rotl(a[2], 12) + rotl(a[3], 18);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h = (h ^ xx_round(0, a[i])) * XXP1 + XXP4;
+    } else {
+        h = XXP5;
+    }
+    h += len;
+    const uint8_t *tp = src + sbytes;
+    uint32_t rem = (uint32_t)(len - sbytes);
+    while (rem >= 8) {
+        const uint64_t w = ldg_u64(tp);
+        h ^= xx_round(0, w);
+        h = rotl(h, 27) * XXP1 + XXP4;
+        zor |= w;
+        if (CENSUS) cmin = min(cmin, census_pre(ca, w));
+        tp += 8;
+        rem -= 8;
+    }
+    if (rem >= 4) {
+        const uint32_t w = __ldg(reinterpret_cast<const unsigned int *>(tp));
+        h ^= (uint64_t)w * XXP1;
+        h = rotl(h, 23) * XXP2 + XXP3;
+        zor |= w;
+        tp += 4;
+        rem -= 4;
+    }
+    while (rem) {
+        const uint32_t bb = __ldg(tp);
+        h ^= (uint64_t)bb * XXP5;
+        h = rotl(h, 11) * XXP1;
+        zor |= bb;
+        ++tp;
+        --rem;
+    }
+    h ^= h >> 33;
+    h *= XXP2;
+    h ^= h >> 29;
+    h *= XXP3;
+    h ^= h >> 32;
+    r.hash = h;
+    r.zero = zor == 0;
+    r.cand = CENSUS && cmin <= ca.pre_span && len >= 8;
+    return r;
+}
+
+}  // namespace kc

@@ -1,203 +1,28 @@
 // k_compare.cu -- per-dtype comparison of replayed outputs against captured
 // ones (Section "Replay Validation": byte-exact and numpy.allclose-style
-// tolerance comparison, NaNs reported explicitly).
+// tolerance comparison, NaNs reported explicitly); the element logic is in
+// compare_tile.cuh.
 //
-// All pairs are cut into 64 KiB tiles of `got` bytes, flattened into one tile
-// space; a persistent grid walks it.  Each thread streams 16-byte vectors of
-// both buffers.  A vector whose 16 bytes are bitwise equal in got and want
-// only needs its NaNs counted (equal bits are equal values, NaN == NaN), so
-// the FP64 unit -- slow on this part -- is used only for elements whose bits
-// differ: those are widened exactly to double, and the error values are one
-// IEEE operation each (__dsub_rn, __ddiv_rn, __dmul_rn, __dadd_rn: no FMA
-// contraction), hence identical to any other correctly rounded evaluation.
-// Per-tile partial results are merged with order-independent atomics: sums
-// of counts, min of the first index (u64, initial all-ones = -1 as i64) and
-// max of the non-negative FP64 maxima as u64 bit patterns (their order is
-// the numeric order; NaN is never stored).
-#include <cuda_fp16.h>
+// All pairs are cut into 16 KiB tiles of `got` bytes, flattened into one
+// tile space; each CTA takes a contiguous range of tiles.  Per-tile partial
+// results are merged with order-independent atomics: sums of counts, min of
+// the first index (u64, initial all-ones = -1 as i64) and max of the
+// non-negative FP64 maxima as u64 bit patterns (their order is the numeric
+// order; NaN is never stored).
 #include <cuda_runtime.h>
-#include <math_constants.h>
 
-#include "kc_device.cuh"
+#include "compare_tile.cuh"
 #include "kc_internal.cuh"
 
 namespace kc {
 
 constexpr int CMP_THREADS = 256;
 
-struct CmpAcc {
-    unsigned long long mism, first, nan_g, nan_w, nan_m;
-    double max_abs, max_rel;
-};
-
-template <int DT>
-__device__ __forceinline__ double widen(uint32_t bits) {
-    if (DT == KC_F32) return (double)__uint_as_float(bits);
-    if (DT == KC_BF16) return (double)__uint_as_float(bits << 16);
-    if (DT == KC_F16) return (double)__half2float(__ushort_as_half((unsigned short)bits));
-    if (DT == KC_I32) return (double)(int32_t)bits;
-    return (double)bits;   // KC_U8 / KC_RAW
-}
-
-// NaN test on the raw bits of one element.
-template <int DT>
-__device__ __forceinline__ bool bits_nan(uint32_t bits) {
-    if (DT == KC_F32) return (bits & 0x7fffffffu) > 0x7f800000u;
-    if (DT == KC_BF16) return (bits & 0x7fffu) > 0x7f80u;
-    if (DT == KC_F16) return (bits & 0x7fffu) > 0x7c00u;
-    return false;
-}
-
-template <int DT>
-__device__ __forceinline__ void cmp_slow(uint32_t gb, uint32_t wb, unsigned long long idx, double atol,
-                                         double rtol, CmpAcc &acc) {
-    const double a = widen<DT>(gb), b = widen<DT>(wb);
-    const bool na = isnan(a), nb = isnan(b);
-    acc.nan_g += na;
-    acc.nan_w += nb;
-    if (na && nb) return;
-    if (na != nb) {
-        acc.mism += 1;
-        acc.nan_m += 1;
-        acc.first = idx < acc.first ? idx : acc.first;
-        return;
-    }
-    if (a == b) return;
-    const double d = fabs(__dsub_rn(a, b));
-    const double r = (b == 0.0 || isinf(d)) ? CUDART_INF : __ddiv_rn(d, fabs(b));
-    acc.max_abs = d > acc.max_abs ? d : acc.max_abs;
-    acc.max_rel = r > acc.max_rel ? r : acc.max_rel;
-    const bool mis = isinf(a) || isinf(b) || d > __dadd_rn(atol, __dmul_rn(rtol, fabs(b)));
-    if (mis) {
-        acc.mism += 1;
-        acc.first = idx < acc.first ? idx : acc.first;
-    }
-}
-
-template <int DT>
-constexpr int esize() {
-    return DT == KC_F32 || DT == KC_I32 ? 4 : DT == KC_F16 || DT == KC_BF16 ? 2 : 1;
-}
-
-// Element j (0-based) of a 32-bit word.
-template <int DT>
-__device__ __forceinline__ uint32_t elem_of(uint32_t w, int j) {
-    if (esize<DT>() == 4) return w;
-    if (esize<DT>() == 2) return (w >> (16 * j)) & 0xffffu;
-    return (w >> (8 * j)) & 0xffu;
-}
-
-// NaNs in a word whose got and want bits are identical.
-template <int DT>
-__device__ __forceinline__ uint32_t word_nans(uint32_t w) {
-    if (DT == KC_F32) return bits_nan<DT>(w);
-    if (DT == KC_BF16 || DT == KC_F16) return bits_nan<DT>(w & 0xffffu) + bits_nan<DT>(w >> 16);
-    return 0;
-}
-
-template <int DT>
-__device__ __forceinline__ void cmp_word(uint32_t g, uint32_t w, unsigned long long first_elem,
-                                         double atol, double rtol, CmpAcc &acc) {
-    constexpr int per = 4 / esize<DT>();
-    if (g == w) {
-        const uint32_t n = word_nans<DT>(g);
-        acc.nan_g += n;
-        acc.nan_w += n;
-        return;
-    }
-#pragma unroll
-    for (int j = 0; j < per; ++j) {
-        const uint32_t ge = elem_of<DT>(g, j), we = elem_of<DT>(w, j);
-        if (ge == we) {
-            const uint32_t n = bits_nan<DT>(ge);
-            acc.nan_g += n;
-            acc.nan_w += n;
-        } else {
-            cmp_slow<DT>(ge, we, first_elem + j, atol, rtol, acc);
-        }
-    }
-}
-
-template <int DT>
-__device__ __forceinline__ void cmp_vec(uint4 g, uint4 w, unsigned long long first_elem, double atol,
-                                        double rtol, CmpAcc &acc) {
-    constexpr int per = 4 / esize<DT>();
-    if (g.x == w.x && g.y == w.y && g.z == w.z && g.w == w.w) {
-        if (DT == KC_F32 || DT == KC_F16 || DT == KC_BF16) {
-            const uint32_t n = word_nans<DT>(g.x) + word_nans<DT>(g.y) + word_nans<DT>(g.z) +
-                               word_nans<DT>(g.w);
-            acc.nan_g += n;
-            acc.nan_w += n;
-        }
-        return;
-    }
-    cmp_word<DT>(g.x, w.x, first_elem, atol, rtol, acc);
-    cmp_word<DT>(g.y, w.y, first_elem + per, atol, rtol, acc);
-    cmp_word<DT>(g.z, w.z, first_elem + 2 * per, atol, rtol, acc);
-    cmp_word<DT>(g.w, w.w, first_elem + 3 * per, atol, rtol, acc);
-}
-
-// One 64 KiB tile of one pair.
-template <int DT>
-__device__ void cmp_tile(const CmpPair &pr, uint64_t tile_in_pair, double atol, double rtol, CmpAcc &acc) {
-    constexpr int ES = esize<DT>();
-    const uint64_t nbytes = pr.nelem * ES;
-    const uint64_t t0 = tile_in_pair * CMP_TILE_BYTES;
-    const uint64_t tlen = nbytes - t0 < CMP_TILE_BYTES ? nbytes - t0 : CMP_TILE_BYTES;
-    const uint8_t *g = reinterpret_cast<const uint8_t *>(pr.got) + t0;
-    const uint8_t *w = reinterpret_cast<const uint8_t *>(pr.want) + t0;
-    const uint64_t nvec = tlen >> 4;
-    uint64_t v = threadIdx.x;
-    for (; v + 3 * CMP_THREADS < nvec; v += 4 * CMP_THREADS) {
-        uint4 gv[4], wv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            gv[j] = ldg_stream(g + 16 * (v + j * CMP_THREADS));
-            wv[j] = ldg_stream(w + 16 * (v + j * CMP_THREADS));
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            cmp_vec<DT>(gv[j], wv[j], (t0 + 16 * (v + j * CMP_THREADS)) / ES, atol, rtol, acc);
-    }
-    for (; v < nvec; v += CMP_THREADS) {
-        uint4 gv = ldg_stream(g + 16 * v), wv = ldg_stream(w + 16 * v);
-        cmp_vec<DT>(gv, wv, (t0 + 16 * v) / ES, atol, rtol, acc);
-    }
-    // ragged end of the pair: fewer than 16 bytes, element by element
-    const uint64_t tail0 = nvec << 4;
-    for (uint64_t b = tail0 + (uint64_t)threadIdx.x * ES; b < tlen; b += (uint64_t)CMP_THREADS * ES) {
-        uint32_t gb = 0, wb = 0;
-        for (int j = 0; j < ES; ++j) {
-            gb |= (uint32_t)g[b + j] << (8 * j);
-            wb |= (uint32_t)w[b + j] << (8 * j);
-        }
-        if (gb == wb) {
-            const uint32_t n = bits_nan<DT>(gb);
-            acc.nan_g += n;
-            acc.nan_w += n;
-        } else {
-            cmp_slow<DT>(gb, wb, (t0 + b) / ES, atol, rtol, acc);
-        }
-    }
-}
-
 __global__ void cmp_init_kernel(const CmpPair *__restrict__ pairs, int npairs, kc_cmp_result *__restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npairs) return;
-    kc_cmp_result r;
-    r.mismatches = 0;
-    r.first = -1;
-    r.max_abs = 0.0;
-    r.max_rel = 0.0;
-    r.nan_got = 0;
-    r.nan_want = 0;
-    r.nan_mismatch = 0;
-    r.status = pairs[i].lost ? KC_EBUF : KC_OK;
-    r.reserved = 0;
-    out[i] = r;
+    cmp_record_init(&out[i], pairs[i].lost ? KC_EBUF : KC_OK);
 }
-
-__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 // Merge one CTA's accumulators into the pair's record (all threads call it).
 __device__ void cmp_flush(CmpAcc &acc, kc_cmp_result *o, unsigned long long (*red)[CMP_THREADS / 32]) {
@@ -273,14 +98,7 @@ __global__ void __launch_bounds__(CMP_THREADS) cmp_kernel(const CmpPair *__restr
         }
         if (moved) pr = pairs[k];
         if (pr.lost) continue;
-        const uint64_t tip = tile - pr.tile_first;
-        switch (pr.dtype) {
-        case KC_F32: cmp_tile<KC_F32>(pr, tip, atol, rtol, acc); break;
-        case KC_F16: cmp_tile<KC_F16>(pr, tip, atol, rtol, acc); break;
-        case KC_BF16: cmp_tile<KC_BF16>(pr, tip, atol, rtol, acc); break;
-        case KC_I32: cmp_tile<KC_I32>(pr, tip, atol, rtol, acc); break;
-        default: cmp_tile<KC_U8>(pr, tip, atol, rtol, acc); break;
-        }
+        cmp_tile_any(pr, tile - pr.tile_first, atol, rtol, acc, threadIdx.x, CMP_THREADS);
     }
     cmp_flush(acc, &out[k], red);
 }

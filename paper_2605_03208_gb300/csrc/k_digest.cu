@@ -1,34 +1,10 @@
-// k_digest.cu -- page digest (XXH64 seed 0 + zero flag), optionally fused
-// with the pointer-census pre-filter, and the census count / write / scan
-// kernels.
-//
-// Digest mapping.  XXH64 keeps four serial accumulators, one per 8-byte lane
-// of every 32-byte stripe, so one page is hashed by a quad of four threads
-// (thread k owns accumulator k).  A warp hashes eight pages at once (one per
-// quad) and takes its next eight pages from a global ticket counter, so
-// warps that finish early steal the remaining work.  Each warp owns a ring of
-// `stages` shared-memory stages; a stage holds one `chunk` of each of its
-// pages.  The threads of a page copy its chunk with per-thread 16-byte
-// asynchronous copies (cp.async), one commit group per stage, and wait for
-// the group before hashing it.  (One bulk TMA copy per page per stage moves
-// the same bytes, but issuing eight of them per chunk stalled the issuing
-// warp for ~900 cycles -- time it could not spend hashing -- while the
-// per-thread copies never block.)  Page slots are padded by 32 bytes so the
-// eight pages' shared loads spread over all 32 banks.  The < 32-byte tail of
-// a page is read from global memory by the page leader while it finishes the
-// hash.
-//
-// The serial chain per accumulator is the critical path: each step is an
-// add, a rotate and a multiply by PRIME1 (xx_step); the lane products
-// (lane * PRIME2) and the next stripes' shared loads are issued ahead of it.
-//
-// Census when fused: the hashing loop only keeps, per page, the minimum of
-// (high 32 bits of a word - pre_lo), a branch-free conservative test of
-// whether any word can be a hit.  Pages that pass are classified afterwards
-// by census_flagged_kernel, one word per lane, so a pointer-dense page never
-// holds up the hashing warps.
+// k_digest.cu -- the page digest kernel (XXH64 seed 0 + zero flag, optionally
+// with the census pre-filter flag per page; hashing in digest_task.cuh) and
+// the census kernels: classification of flagged pages, the standalone count
+// pass, the ordered write pass, and a single-CTA scan.
 #include <cuda_runtime.h>
 
+#include "digest_task.cuh"
 #include "kc_device.cuh"
 #include "kc_internal.cuh"
 
@@ -42,247 +18,50 @@ size_t digest_smem_bytes(const DigestShape &s) {
     return (size_t)s.warps * s.stages * ppw * (size_t)(s.chunk + 32);
 }
 
-// CHUNK = the chunk size as a compile-time constant (0: runtime only); full
-// chunks of that size take a fully unrolled path.
-// LPT = XXH64 lanes per thread.  LPT = 1: four threads per page (8 pages per
-// warp), the most parallel layout, for few pages.  LPT = 2: two threads per
-// page, each owning two adjacent lanes (one 16-byte shared load per stripe
-// feeds two independent chains), 16 pages per warp: half the instructions
-// per byte and twice the instruction-level parallelism, for many pages.
+// One warp per task of PPW consecutive pages (8 with one XXH64 lane per
+// thread, 16 with two), tasks taken from a global ticket counter so warps
+// that finish early steal the rest; see digest_task.cuh for the hashing.
 template <bool CENSUS, int LPT, int CHUNK>
 __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, uint64_t *__restrict__ hash,
                                                      uint8_t *__restrict__ zero,
                                                      uint32_t *__restrict__ page_hits,
                                                      uint32_t *__restrict__ task_ctr,
                                                      uint32_t *__restrict__ status, int stages, int chunk) {
-    constexpr int TPP = 4 / LPT;    // threads per page
-    constexpr int PPW = 32 / TPP;   // pages per warp task
+    constexpr int TPP = 4 / LPT;
+    constexpr int PPW = 32 / TPP;
     extern __shared__ __align__(128) uint8_t smem[];
-    (void)status;                   // no waits here can time out: cp.async groups always complete
+    (void)status;   // no waits here can time out: cp.async groups always complete
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
-    const int q = lane / TPP;       // page slot of this thread
-    const int j = lane % TPP;       // this thread owns lanes j*LPT .. j*LPT+LPT-1
-    const uint32_t FULL = 0xffffffffu;
-
-    const size_t slot_stride = (size_t)chunk + 32;
-    const size_t stage_stride = PPW * slot_stride;
-    uint8_t *ring = smem + (size_t)warp * stages * stage_stride;
-
+    uint8_t *ring = smem + (size_t)warp * stages * PPW * ((size_t)chunk + 32);
     while (true) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(task_ctr, 1u);
-        t = __shfl_sync(FULL, t, 0);
+        t = __shfl_sync(0xffffffffu, t, 0);
         const uint64_t p0 = (uint64_t)t * PPW;
         if (p0 >= pg.npages) break;
-        const uint64_t p = p0 + q;
+        const uint64_t p = p0 + lane / TPP;
         const bool valid = p < pg.npages;
-
         const uint8_t *src = nullptr;
         uint64_t len = 0;
         bool lost = false;
         if (valid) {
-            const int region = region_of(pg.regions, pg.nregions, p);
-            const Region r = pg.regions[region];
+            const Region r = pg.regions[region_of(pg.regions, pg.nregions, p)];
             const uint64_t off = (p - r.first) << pg.log2page;
             len = r.bytes - off < pg.page ? r.bytes - off : pg.page;
             src = reinterpret_cast<const uint8_t *>(r.base + off);
             lost = r.lost != 0;
         }
-        const uint32_t sbytes = lost ? 0u : (uint32_t)(len & ~31ull);   // bytes in full stripes
-        const uint32_t nch = (sbytes + chunk - 1) / chunk;
-        const uint32_t maxch = __reduce_max_sync(FULL, nch);
-
-        // Copy chunk c of this thread's page into stage c % stages: the
-        // page's threads split its 16-byte pieces.  Every thread commits one
-        // group per call (empty past the page's end), so group counts agree.
-        auto issue = [&](uint32_t c) {
-            if (c < nch) {
-                const uint32_t rest = sbytes - c * chunk;
-                const uint32_t b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
-                uint8_t *dst = ring + (c % stages) * stage_stride + q * slot_stride;
-                const uint8_t *from = src + (size_t)c * chunk;
-                for (uint32_t o = 16 * j; o < b; o += 16 * TPP) cp_async16(dst + o, from + o);
-            }
-            cp_async_commit();
-        };
-        for (int c = 0; c < stages - 1; ++c) issue((uint32_t)c);
-
-        uint64_t acc[LPT];
-#pragma unroll
-        for (int i = 0; i < LPT; ++i) acc[i] = xx_init(j * LPT + i);
-        uint32_t zlo = 0, zhi = 0;
-        uint32_t cmin = 0xFFFFFFFFu;   // census pre-filter, minimum over the page
-        for (uint32_t c = 0; c < maxch; ++c) {
-            issue(c + stages - 1);        // refills the stage consumed in the previous iteration
-            cp_async_wait(stages - 1);    // this thread's pieces of chunk c have landed
-            __syncwarp();                 // ... and so have those of the page's other threads
-            const int st = (int)(c % stages);
-            uint32_t b = 0;
-            if (c < nch) {
-                const uint32_t rest = sbytes - c * chunk;
-                b = rest < (uint32_t)chunk ? rest : (uint32_t)chunk;
-            }
-            const uint8_t *slot = ring + st * stage_stride + q * slot_stride + 8 * LPT * j;
-            // one load per stripe: LPT consecutive 8-byte lanes
-            auto ld = [&](uint32_t off, uint64_t (&w)[LPT]) {
-                if (LPT == 1) {
-                    w[0] = *reinterpret_cast<const uint64_t *>(slot + off);
-                } else {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(slot + off);
-                    w[0] = ((uint64_t)v.y << 32) | v.x;
-                    w[LPT - 1] = ((uint64_t)v.w << 32) | v.z;
-                }
-            };
-            auto eat = [&](const uint64_t (&w)[LPT]) {
-#pragma unroll
-                for (int i = 0; i < LPT; ++i) {
-                    zlo |= (uint32_t)w[i];
-                    zhi |= (uint32_t)(w[i] >> 32);
-                    if (CENSUS) cmin = min(cmin, census_pre(ca, w[i]));
-                }
-            };
-            uint32_t s = 0;
-            if (CHUNK && b == (uint32_t)CHUNK) {
-                // a full chunk of compile-time size: fully unrolled, the
-                // loads of all its stripes issued ahead of the chains
-                uint64_t w[4][LPT];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) ld(32 * u, w[u]);
-#pragma unroll
-                for (int g = 0; g < CHUNK / 128; ++g) {
-                    uint64_t nw[4][LPT];
-                    if (g + 1 < CHUNK / 128) {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) ld(128 * (g + 1) + 32 * u, nw[u]);
-                    }
-                    uint64_t m[4][LPT];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int i = 0; i < LPT; ++i) m[u][i] = w[u][i] * XXP2;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], m[u][i]);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) eat(w[u]);
-                    if (g + 1 < CHUNK / 128) {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-#pragma unroll
-                            for (int i = 0; i < LPT; ++i) w[u][i] = nw[u][i];
-                    }
-                }
-                s = b;
-            } else if (b >= 128) {
-                // register double buffer: the next four stripes are loaded
-                // while the current four run through the chains
-                uint64_t w[4][LPT];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) ld(32 * u, w[u]);
-                for (; s + 128 <= b; s += 128) {
-                    const uint32_t ns = (s + 256 <= b) ? s + 128 : s;   // last group reloads itself
-                    uint64_t nw[4][LPT];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) ld(ns + 32 * u, nw[u]);
-                    uint64_t m[4][LPT];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int i = 0; i < LPT; ++i) m[u][i] = w[u][i] * XXP2;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], m[u][i]);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) eat(w[u]);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int i = 0; i < LPT; ++i) w[u][i] = nw[u][i];
-                }
-            }
-            for (; s < b; s += 32) {
-                uint64_t w[LPT];
-                ld(s, w);
-#pragma unroll
-                for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], w[i] * XXP2);
-                eat(w);
-            }
-            __syncwarp();                 // the stage is free for the next refill
-        }
-        cp_async_wait(0);                 // trailing (empty) groups
-
-        // Page reduction: accumulators to the page leader, OR of bytes, census flag.
-        const int lead = lane - j;
-        uint64_t a[4];
-        if (LPT == 1) {
-            a[0] = acc[0];
-#pragma unroll
-            for (int i = 1; i < 4; ++i) a[i] = __shfl_sync(FULL, acc[0], lead + i);
-        } else {
-            a[0] = acc[0];
-            a[1] = acc[LPT - 1];
-            a[2] = __shfl_sync(FULL, acc[0], lead + 1);
-            a[3] = __shfl_sync(FULL, acc[LPT - 1], lead + 1);
-        }
-        uint64_t zor = ((uint64_t)zhi << 32) | zlo;
-#pragma unroll
-        for (int o = 1; o < TPP; o <<= 1) {
-            zor |= __shfl_xor_sync(FULL, zor, o);
-            if (CENSUS) cmin = min(cmin, __shfl_xor_sync(FULL, cmin, o));
-        }
-        if (j == 0 && valid) {
+        const PageDigest d = digest_pages<CENSUS, LPT, CHUNK>(ring, stages, chunk, src, len, lost, ca);
+        if (lane % TPP == 0 && valid) {
             if (lost) {
                 hash[p] = 0;
                 zero[p] = KC_PAGE_LOST;
                 if (CENSUS) page_hits[p] = 0;
             } else {
-                uint64_t h;
-                if (len >= 32) {
-                    h = rotl(a[0], 1) + rotl(a[1], 7) + rotl(a[2], 12) + rotl(a[3], 18);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) h = (h ^ xx_round(0, a[i])) * XXP1 + XXP4;
-                } else {
-                    h = XXP5;
-                }
-                h += len;
-                const uint8_t *tp = src + sbytes;
-                uint32_t rem = (uint32_t)(len - sbytes);
-                while (rem >= 8) {
-                    const uint64_t w = ldg_u64(tp);
-                    h ^= xx_round(0, w);
-                    h = rotl(h, 27) * XXP1 + XXP4;
-                    zor |= w;
-                    if (CENSUS) cmin = min(cmin, census_pre(ca, w));
-                    tp += 8;
-                    rem -= 8;
-                }
-                if (rem >= 4) {
-                    const uint32_t w = __ldg(reinterpret_cast<const unsigned int *>(tp));
-                    h ^= (uint64_t)w * XXP1;
-                    h = rotl(h, 23) * XXP2 + XXP3;
-                    zor |= w;
-                    tp += 4;
-                    rem -= 4;
-                }
-                while (rem) {
-                    const uint32_t bb = __ldg(tp);
-                    h ^= (uint64_t)bb * XXP5;
-                    h = rotl(h, 11) * XXP1;
-                    zor |= bb;
-                    ++tp;
-                    --rem;
-                }
-                h ^= h >> 33;
-                h *= XXP2;
-                h ^= h >> 29;
-                h *= XXP3;
-                h ^= h >> 32;
-                hash[p] = h;
-                zero[p] = zor == 0 ? KC_PAGE_ZERO : KC_PAGE_DATA;
-                if (CENSUS) page_hits[p] = (cmin <= ca.pre_span && len >= 8) ? HITS_PENDING : 0u;
+                hash[p] = d.hash;
+                zero[p] = d.zero ? KC_PAGE_ZERO : KC_PAGE_DATA;
+                if (CENSUS) page_hits[p] = d.cand ? HITS_PENDING : 0u;
             }
         }
     }

@@ -28,7 +28,8 @@ namespace kc {
 cudaError_t setup_kernels() {
     cudaError_t e = setup_digest_kernels();
     if (e != cudaSuccess) return e;
-    return setup_dedup_kernels();
+    if ((e = setup_dedup_kernels()) != cudaSuccess) return e;
+    return setup_batch_kernels();
 }
 
 static std::atomic<uint64_t> g_launches{0};
@@ -39,26 +40,50 @@ uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); 
 namespace {
 
 constexpr uint32_t CENSUS_UNIT = 64 * 1024;
-constexpr size_t TABLE_CACHE = 32;
+constexpr size_t TABLE_CACHE = 64;
 
-enum TableKind : uint32_t { TK_PAGES = 1, TK_UNITS = 2, TK_TARGETS = 3, TK_PAIRS = 4 };
+enum TableKind : uint32_t { TK_PAGES = 1, TK_UNITS = 2, TK_TARGETS = 3, TK_PAIRS = 4, TK_BATCH = 5 };
+
+// Pinned host + device buffer pair holding one table set; recycled through
+// the context's free list instead of being freed (a cudaFree would wait for
+// the whole device).  `used` is recorded after every call that reads it.
+struct TableBuf {
+    void *d = nullptr;
+    void *h = nullptr;
+    size_t cap = 0;
+    cudaEvent_t used = nullptr;
+};
+
+enum TablePart { TP_REGIONS = 0, TP_PAGEFIRST, TP_RANGES, TP_PAIRS, TP_JOBS, TP_WORK, TP_COUNT };
 
 // A device-resident table set for one descriptor list.
 struct Tables {
     std::vector<uint8_t> key;
-    void *d = nullptr;          // device copy
-    void *h = nullptr;          // pinned host copy, source of the upload
-    size_t bytes = 0;
-    const Region *regions = nullptr;
-    const uint64_t *page_first = nullptr;
-    const Range *ranges = nullptr;
-    const CmpPair *pairs = nullptr;
+    TableBuf buf;
+    const void *part[TP_COUNT] = {};   // device address of each uploaded part
     int n = 0;
     uint64_t units = 0;         // pages, census units or comparison tiles
+    uint64_t items = 0;         // batched form: work items
+    int nranges = 0;            // batched form: ranges
     bool any_lost = false;
+    bool pinned = false;        // read by a captured graph: never recycled
     std::vector<int> buf_status;
     CensusArgs ca{};
+    const Region *regions() const { return static_cast<const Region *>(part[TP_REGIONS]); }
+    const uint64_t *page_first() const { return static_cast<const uint64_t *>(part[TP_PAGEFIRST]); }
+    const Range *ranges() const { return static_cast<const Range *>(part[TP_RANGES]); }
+    const CmpPair *pairs() const { return static_cast<const CmpPair *>(part[TP_PAIRS]); }
+    const BatchJob *jobs() const { return static_cast<const BatchJob *>(part[TP_JOBS]); }
+    const BatchRange *work() const { return static_cast<const BatchRange *>(part[TP_WORK]); }
 };
+
+using HostParts = std::vector<uint8_t>[TP_COUNT];
+
+template <class T>
+void put(std::vector<uint8_t> &dst, const std::vector<T> &v) {
+    dst.resize(v.size() * sizeof(T));
+    if (!v.empty()) memcpy(dst.data(), v.data(), dst.size());
+}
 
 }  // namespace
 
@@ -72,6 +97,7 @@ struct kc_ctx {
     void *d_scratch = nullptr;
     size_t scratch_cap = 0;
     std::list<Tables> tables;     // most recently used first
+    std::vector<TableBuf> free_bufs;
     DigestShape forced{0, 0, 0, 0, 0};
     cudaEvent_t trace_start = nullptr;   // caller-owned, recorded around main kernels
     cudaEvent_t trace_stop = nullptr;
@@ -206,16 +232,47 @@ CensusArgs make_census(const std::vector<Range> &rg, uint64_t win_lo, uint64_t w
     return ca;
 }
 
-void free_tables(Tables &t) {
-    if (t.d) cudaFree(t.d);        // synchronises with queued kernels that read it
-    if (t.h) cudaFreeHost(t.h);
-    t.d = t.h = nullptr;
+void destroy_buf(TableBuf &b) {
+    if (b.d) cudaFree(b.d);
+    if (b.h) cudaFreeHost(b.h);
+    if (b.used) cudaEventDestroy(b.used);
+    b = TableBuf{};
 }
 
-// Find the tables for `key`, or build them with `fill` (which appends the
-// host parts and sets the derived fields) and upload them on `st`.
+// Return an entry's buffer to the free list once the GPU is done with it.
+void recycle(kc_ctx *c, Tables &t) {
+    if (t.buf.used) cudaEventSynchronize(t.buf.used);
+    c->free_bufs.push_back(t.buf);
+    t.buf = TableBuf{};
+}
+
+kc_status acquire_buf(kc_ctx *c, size_t bytes, TableBuf *out) {
+    size_t best = (size_t)-1;
+    for (size_t i = 0; i < c->free_bufs.size(); ++i)
+        if (c->free_bufs[i].cap >= bytes && (best == (size_t)-1 || c->free_bufs[i].cap < c->free_bufs[best].cap))
+            best = i;
+    if (best != (size_t)-1) {
+        *out = c->free_bufs[best];
+        c->free_bufs.erase(c->free_bufs.begin() + best);
+        return KC_OK;
+    }
+    TableBuf b;
+    b.cap = 64 * 1024;
+    while (b.cap < bytes) b.cap *= 2;
+    if (cudaHostAlloc(&b.h, b.cap, cudaHostAllocDefault) != cudaSuccess || cudaMalloc(&b.d, b.cap) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.used, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_buf(b);
+        return fail(c, KC_ENOMEM, "table buffer allocation of %zu bytes failed", bytes);
+    }
+    *out = b;
+    return KC_OK;
+}
+
+// Find the tables for `key`, or build them with `fill` (which fills the host
+// parts and the derived fields) and upload them on `st`.
 template <class Fill>
-kc_status tables_for(kc_ctx *c, std::vector<uint8_t> &&key, cudaStream_t st, Fill fill, const Tables **out) {
+kc_status tables_for(kc_ctx *c, std::vector<uint8_t> &&key, cudaStream_t st, Fill fill, Tables **out) {
     for (auto it = c->tables.begin(); it != c->tables.end(); ++it) {
         if (it->key == key) {
             c->tables.splice(c->tables.begin(), c->tables, it);
@@ -226,49 +283,50 @@ kc_status tables_for(kc_ctx *c, std::vector<uint8_t> &&key, cudaStream_t st, Fil
     }
     Tables t;
     t.key = std::move(key);
-    std::vector<Region> regions;
-    std::vector<uint64_t> pf;
-    std::vector<Range> rg;
-    std::vector<CmpPair> pairs;
-    kc_status s = fill(t, regions, pf, rg, pairs);
+    HostParts parts;
+    kc_status s = fill(t, parts);
     if (s != KC_OK) return s;
     if (capturing(st))
         return fail(c, KC_ENOMEM, "region tables must be built before a stream capture: make one uncaptured call "
                                   "with the same descriptors first");
-    auto rup = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t o_reg = 0, o_pf = o_reg + rup(regions.size() * sizeof(Region));
-    const size_t o_rg = o_pf + rup(pf.size() * 8), o_pr = o_rg + rup(rg.size() * sizeof(Range));
-    t.bytes = o_pr + rup(pairs.size() * sizeof(CmpPair));
-    if (t.bytes == 0) t.bytes = 256;
-    KC_CHECK(c, cudaHostAlloc(&t.h, t.bytes, cudaHostAllocDefault), "pinned table allocation");
-    if (cudaMalloc(&t.d, t.bytes) != cudaSuccess) {
-        cudaFreeHost(t.h);
-        cudaGetLastError();
-        return fail(c, KC_ENOMEM, "device table allocation of %zu bytes failed", t.bytes);
+    size_t off[TP_COUNT], total = 0;
+    for (int i = 0; i < TP_COUNT; ++i) {
+        off[i] = total;
+        total += (parts[i].size() + 255) & ~size_t(255);
     }
-    char *h = static_cast<char *>(t.h), *d = static_cast<char *>(t.d);
-    if (!regions.empty()) memcpy(h + o_reg, regions.data(), regions.size() * sizeof(Region));
-    if (!pf.empty()) memcpy(h + o_pf, pf.data(), pf.size() * 8);
-    if (!rg.empty()) memcpy(h + o_rg, rg.data(), rg.size() * sizeof(Range));
-    if (!pairs.empty()) memcpy(h + o_pr, pairs.data(), pairs.size() * sizeof(CmpPair));
-    t.regions = regions.empty() ? nullptr : reinterpret_cast<const Region *>(d + o_reg);
-    t.page_first = pf.empty() ? nullptr : reinterpret_cast<const uint64_t *>(d + o_pf);
-    t.ranges = rg.empty() ? nullptr : reinterpret_cast<const Range *>(d + o_rg);
-    t.pairs = pairs.empty() ? nullptr : reinterpret_cast<const CmpPair *>(d + o_pr);
-    t.ca.ranges = t.ranges;
-    cudaError_t e = cudaMemcpyAsync(t.d, t.h, t.bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-        free_tables(t);
-        return cuda_fail(c, e, "table upload");
-    }
+    if (total == 0) total = 256;
     if (c->tables.size() >= TABLE_CACHE) {
-        free_tables(c->tables.back());
-        c->tables.pop_back();
+        for (auto it = c->tables.rbegin(); it != c->tables.rend(); ++it) {
+            if (!it->pinned) {
+                recycle(c, *it);
+                c->tables.erase(std::next(it).base());
+                break;
+            }
+        }
+    }
+    if ((s = acquire_buf(c, total, &t.buf)) != KC_OK) return s;
+    char *h = static_cast<char *>(t.buf.h), *d = static_cast<char *>(t.buf.d);
+    for (int i = 0; i < TP_COUNT; ++i) {
+        if (!parts[i].empty()) memcpy(h + off[i], parts[i].data(), parts[i].size());
+        t.part[i] = parts[i].empty() ? nullptr : d + off[i];
+    }
+    t.ca.ranges = t.ranges();
+    cudaError_t e = cudaMemcpyAsync(t.buf.d, t.buf.h, total, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        c->free_bufs.push_back(t.buf);
+        return cuda_fail(c, e, "table upload");
     }
     c->tables.push_front(std::move(t));
     *out = &c->tables.front();
     c->buf_status = c->tables.front().buf_status;
     return KC_OK;
+}
+
+// After the kernels that read `t` are enqueued: remember when it is free.
+void touch(kc_ctx *c, Tables *t, cudaStream_t st) {
+    if (capturing(st)) t->pinned = true;
+    else cudaEventRecord(t->buf.used, st);
+    (void)c;
 }
 
 std::vector<uint8_t> region_key(TableKind kind, const kc_buf *b, int n, uint64_t a, uint64_t bb, uint64_t cc) {
@@ -283,20 +341,24 @@ std::vector<uint8_t> region_key(TableKind kind, const kc_buf *b, int n, uint64_t
 // Page tables: regions with page offsets at `page`, page_first, and (census)
 // the sorted ranges and census parameters for the window.
 kc_status page_tables(kc_ctx *c, const kc_buf *b, int n, uint32_t page, bool census, uint64_t wlo, uint64_t whi,
-                      cudaStream_t st, const Tables **out) {
+                      cudaStream_t st, Tables **out) {
     if (n < 1 || !b) return fail(c, KC_EINVAL, "need at least one region (n=%d)", n);
     auto key = region_key(census ? TK_UNITS : TK_PAGES, b, n, page, census ? wlo : 0, census ? whi : 0);
     return tables_for(c, std::move(key), st,
-                      [&](Tables &t, std::vector<Region> &regions, std::vector<uint64_t> &pf, std::vector<Range> &rg,
-                          std::vector<CmpPair> &) -> kc_status {
+                      [&](Tables &t, HostParts &parts) -> kc_status {
+                          std::vector<Region> regions;
                           kc_status s = check_regions(c, b, n, page, regions, &t.units, t.buf_status, &t.any_lost);
                           if (s != KC_OK) return s;
-                          pf.resize(n + 1);
+                          std::vector<uint64_t> pf(n + 1);
                           for (int i = 0; i < n; ++i) pf[i] = regions[i].first;
                           pf[n] = t.units;
+                          put(parts[TP_REGIONS], regions);
+                          put(parts[TP_PAGEFIRST], pf);
                           if (census) {
+                              std::vector<Range> rg;
                               if ((s = build_ranges(c, b, n, rg)) != KC_OK) return s;
                               t.ca = make_census(rg, wlo, whi);
+                              put(parts[TP_RANGES], rg);
                           }
                           t.n = n;
                           return KC_OK;
@@ -477,7 +539,8 @@ KC_API void kc_destroy(kc_ctx *c) {
     if (!c) return;
     DevGuard g(c->device);
     cudaDeviceSynchronize();
-    for (auto &t : c->tables) free_tables(t);
+    for (auto &t : c->tables) destroy_buf(t.buf);
+    for (auto &b : c->free_bufs) destroy_buf(b);
     if (c->d_scratch) cudaFree(c->d_scratch);
     if (c->d_misc) cudaFree(c->d_misc);
     delete c;
@@ -545,11 +608,11 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
     if (!d_hash || !d_zero) return fail(c, KC_EINVAL, "null digest output");
     if (census && !d_counts) return fail(c, KC_EINVAL, "null census counts");
     if (census && cap && !d_hits) return fail(c, KC_EINVAL, "null census hit buffer with cap %llu", (unsigned long long)cap);
-    const Tables *t = nullptr;
+    Tables *t = nullptr;
     kc_status s = page_tables(c, allocs, n, page_bytes, census, win_lo, win_hi, st, &t);
     if (s != KC_OK) return s;
     const uint64_t P = t->units;
-    const Pages pg = make_pages(t->regions, n, P, page_bytes);
+    const Pages pg = make_pages(t->regions(), n, P, page_bytes);
     const DigestShape shape = pick_shape(c, page_bytes, P);
     uint32_t *page_hits = nullptr;
     uint64_t *page_off = nullptr;
@@ -568,12 +631,13 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
                  "digest launch");
     }
     if (d_page_first)
-        KC_CHECK(c, cudaMemcpyAsync(d_page_first, t->page_first, (n + 1) * 8, cudaMemcpyDeviceToDevice, st),
+        KC_CHECK(c, cudaMemcpyAsync(d_page_first, t->page_first(), (n + 1) * 8, cudaMemcpyDeviceToDevice, st),
                  "page_first copy");
     if (census) {
         KC_CHECK(c, launch_census_flagged(pg, t->ca, page_hits, d_counts, c->sms, st), "census classify");
         if ((s = census_tail(c, pg, t->ca, page_hits, page_off, d_hits, cap, st)) != KC_OK) return s;
     }
+    touch(c, t, st);
     return lost_status(c, t);
 }
 
@@ -597,11 +661,11 @@ KC_API kc_status kc_census(kc_ctx *c, const kc_buf *allocs, int n, uint64_t win_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!d_counts) return fail(c, KC_EINVAL, "null census counts");
     if (cap && !d_hits) return fail(c, KC_EINVAL, "null census hit buffer with cap %llu", (unsigned long long)cap);
-    const Tables *t = nullptr;
+    Tables *t = nullptr;
     kc_status s = page_tables(c, allocs, n, CENSUS_UNIT, true, win_lo, win_hi, st, &t);
     if (s != KC_OK) return s;
     const uint64_t U = t->units;
-    const Pages units = make_pages(t->regions, n, U, CENSUS_UNIT);
+    const Pages units = make_pages(t->regions(), n, U, CENSUS_UNIT);
     void *scr = nullptr;
     if ((s = scratch(c, U * 4 + 256 + U * 8, st, &scr)) != KC_OK) return s;
     uint32_t *unit_hits = static_cast<uint32_t *>(scr);
@@ -612,6 +676,7 @@ KC_API kc_status kc_census(kc_ctx *c, const kc_buf *allocs, int n, uint64_t win_
         KC_CHECK(c, launch_census_count(units, t->ca, unit_hits, d_counts, c->sms, st), "census count");
     }
     if ((s = census_tail(c, units, t->ca, unit_hits, unit_off, cap ? d_hits : nullptr, cap, st)) != KC_OK) return s;
+    touch(c, t, st);
     return lost_status(c, t);
 }
 
@@ -624,12 +689,12 @@ KC_API kc_status kc_dedup(kc_ctx *c, const kc_buf *allocs, int n, uint32_t page_
     if (!pow2_page(page_bytes)) return fail(c, KC_EINVAL, "page size %u is not a power of two in [4 KiB, 2 MiB]", page_bytes);
     if (!d_hash || !d_zero || !d_table) return fail(c, KC_EINVAL, "null dedup input or table");
     if (d_arena && (reinterpret_cast<uintptr_t>(d_arena) & 15)) return fail(c, KC_EINVAL, "arena is not 16-byte aligned");
-    const Tables *t = nullptr;
+    Tables *t = nullptr;
     kc_status s = page_tables(c, allocs, n, page_bytes, false, 0, 0, st, &t);
     if (s != KC_OK) return s;
     const uint64_t P = t->units;
     if (P >= 0xFFFFFFF0ull) return fail(c, KC_EINVAL, "too many pages (%llu) for 32-bit page ids", (unsigned long long)P);
-    const Pages pg = make_pages(t->regions, n, P, page_bytes);
+    const Pages pg = make_pages(t->regions(), n, P, page_bytes);
     void *scr = nullptr;
     if ((s = scratch(c, dedup_scratch_bytes(P, nullptr), st, &scr)) != KC_OK) return s;
     DedupScratch ds;
@@ -639,6 +704,7 @@ KC_API kc_status kc_dedup(kc_ctx *c, const kc_buf *allocs, int n, uint32_t page_
         KC_CHECK(c, run_dedup(pg, d_hash, d_zero, d_table, d_arena, arena_cap, d_n_blobs, ds, status_word(c), c->sms, st),
                  "dedup");
     }
+    touch(c, t, st);
     return lost_status(c, t);
 }
 
@@ -651,14 +717,15 @@ KC_API kc_status kc_restore(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pag
     if (n_pages && !d_table) return fail(c, KC_EINVAL, "null page table");
     if (arena_bytes && !d_arena) return fail(c, KC_EINVAL, "null arena with %llu bytes", (unsigned long long)arena_bytes);
     if (d_arena && (reinterpret_cast<uintptr_t>(d_arena) & 15)) return fail(c, KC_EINVAL, "arena is not 16-byte aligned");
-    const Tables *t = nullptr;
+    Tables *t = nullptr;
     kc_status s = page_tables(c, allocs, n, page_bytes, false, 0, 0, st, &t);
     if (s != KC_OK) return s;
-    const Pages pg = make_pages(t->regions, n, n_pages, page_bytes);
+    const Pages pg = make_pages(t->regions(), n, n_pages, page_bytes);
     {
         Trace tr(c, st);
         KC_CHECK(c, launch_restore(pg, d_table, n_pages, d_arena, arena_bytes, status_word(c), c->sms, st), "restore");
     }
+    touch(c, t, st);
     return lost_status(c, t);
 }
 
@@ -671,12 +738,11 @@ KC_API kc_status kc_compare(kc_ctx *c, const kc_buf *got, const kc_buf *want, in
     if (!(atol >= 0.0) || !(rtol >= 0.0)) return fail(c, KC_EINVAL, "tolerances must be >= 0 and not NaN");
     auto key = region_key(TK_PAIRS, got, npairs, 0, 0, 0);
     key_add(key, want, (size_t)npairs * sizeof(kc_buf));
-    const Tables *t = nullptr;
+    Tables *t = nullptr;
     kc_status s = tables_for(
         c, std::move(key), st,
-        [&](Tables &tb, std::vector<Region> &, std::vector<uint64_t> &, std::vector<Range> &,
-            std::vector<CmpPair> &pairs) -> kc_status {
-            pairs.resize(npairs);
+        [&](Tables &tb, HostParts &parts) -> kc_status {
+            std::vector<CmpPair> pairs(npairs);
             tb.buf_status.assign(npairs, KC_OK);
             uint64_t tiles = 0;
             for (int k = 0; k < npairs; ++k) {
@@ -702,15 +768,127 @@ KC_API kc_status kc_compare(kc_ctx *c, const kc_buf *got, const kc_buf *want, in
             }
             tb.units = tiles;
             tb.n = npairs;
+            put(parts[TP_PAIRS], pairs);
             return KC_OK;
         },
         &t);
     if (s != KC_OK) return s;
     {
         Trace tr(c, st);
-        KC_CHECK(c, launch_compare(t->pairs, npairs, t->units, atol, rtol, d_out, nullptr, c->sms, st), "compare");
+        KC_CHECK(c, launch_compare(t->pairs(), npairs, t->units, atol, rtol, d_out, nullptr, c->sms, st), "compare");
     }
+    touch(c, t, st);
     return t->any_lost ? fail(c, KC_EBUF, "one or more pairs were marked lost") : KC_OK;
+}
+
+KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t page_bytes, double atol,
+                              double rtol, const kc_work *work, int nwork, void *stream) {
+    if (!c) return KC_EINVAL;
+    DevGuard g(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!pow2_page(page_bytes)) return fail(c, KC_EINVAL, "page size %u is not a power of two in [4 KiB, 2 MiB]", page_bytes);
+    if (njobs < 1 || !jobs) return fail(c, KC_EINVAL, "need at least one job");
+    if (nwork < 0 || (nwork > 0 && !work)) return fail(c, KC_EINVAL, "bad work list");
+    if (!(atol >= 0.0) || !(rtol >= 0.0)) return fail(c, KC_EINVAL, "tolerances must be >= 0 and not NaN");
+    auto key = region_key(TK_BATCH, nullptr, njobs, page_bytes, (uint64_t)nwork, 0);
+    key_add(key, jobs, (size_t)njobs * sizeof(kc_job));
+    if (nwork > 0) key_add(key, work, (size_t)nwork * sizeof(kc_work));
+    Tables *t = nullptr;
+    kc_status s = tables_for(
+        c, std::move(key), st,
+        [&](Tables &tb, HostParts &parts) -> kc_status {
+            std::vector<BatchJob> bj(njobs);
+            std::vector<uint64_t> pages(njobs), items(njobs);
+            tb.buf_status.assign(njobs, KC_OK);
+            for (int k = 0; k < njobs; ++k) {
+                const kc_job &J = jobs[k];
+                const bool dg = (J.flags & KC_JOB_DIGEST) != 0, cm = (J.flags & KC_JOB_COMPARE) != 0;
+                if (!dg && !cm) return fail(c, KC_EINVAL, "job %d asks for neither digest nor compare", k);
+                if (J.bytes == 0 || (J.got_va & 15)) return fail(c, KC_EINVAL, "job %d: empty or misaligned buffer", k);
+                if (dg && (!J.d_hash || !J.d_zero)) return fail(c, KC_EINVAL, "job %d: null digest outputs", k);
+                const int dt = J.dtype;
+                if (dt < KC_U8 || dt > KC_RAW) return fail(c, KC_EINVAL, "job %d has dtype %d", k, dt);
+                const uint64_t es = (dt == KC_F32 || dt == KC_I32) ? 4 : (dt == KC_F16 || dt == KC_BF16) ? 2 : 1;
+                if (cm && (!J.d_cmp || (J.want_va & 15) || J.bytes % es))
+                    return fail(c, KC_EINVAL, "job %d: bad comparison (output, alignment or element size)", k);
+                BatchJob &b = bj[k];
+                b.got = J.got_va;
+                b.want = J.want_va;
+                b.bytes = J.bytes;
+                b.nelem = J.bytes / es;
+                b.hash = J.d_hash;
+                b.zero = J.d_zero;
+                b.cmp = J.d_cmp;
+                b.dtype = dt == KC_RAW ? KC_U8 : dt;
+                b.flags = (dg ? BJ_DIGEST : 0u) | (cm ? BJ_COMPARE : 0u) | ((J.flags & KC_BUF_LOST) ? BJ_LOST : 0u) |
+                          ((work == nullptr || (J.flags & KC_JOB_INIT)) ? BJ_INIT : 0u);
+                if (J.flags & KC_BUF_LOST) {
+                    tb.any_lost = true;
+                    tb.buf_status[k] = KC_EBUF;
+                }
+                pages[k] = (J.bytes + page_bytes - 1) / page_bytes;
+                items[k] = (J.bytes + KC_BATCH_ITEM_BYTES - 1) / KC_BATCH_ITEM_BYTES;
+            }
+            std::vector<BatchRange> rg;
+            auto add = [&](uint32_t job, uint32_t kind, uint64_t first, uint64_t count) {
+                if (count == 0) return;
+                BatchRange r{first, count, 0, job, kind};
+                rg.push_back(r);
+            };
+            if (nwork == 0) {
+                // largest jobs first; a job's digest range, then its comparison range
+                std::vector<int> order(njobs);
+                for (int k = 0; k < njobs; ++k) order[k] = k;
+                std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].bytes > jobs[b].bytes; });
+                for (int k : order) {
+                    if (bj[k].flags & BJ_DIGEST) add((uint32_t)k, 0, 0, pages[k]);
+                    if (bj[k].flags & BJ_COMPARE) add((uint32_t)k, 1, 0, items[k]);
+                }
+            } else {
+                for (int w = 0; w < nwork; ++w) {
+                    const kc_work &W = work[w];
+                    if (W.job >= (uint32_t)njobs) return fail(c, KC_EINVAL, "work %d: job %u out of range", w, W.job);
+                    const BatchJob &b = bj[W.job];
+                    if (W.kind == KC_WORK_DIGEST) {
+                        if (!(b.flags & BJ_DIGEST) || W.first + W.count > pages[W.job] || W.first + W.count < W.first)
+                            return fail(c, KC_EINVAL, "work %d: digest range outside job %u", w, W.job);
+                    } else if (W.kind == KC_WORK_COMPARE) {
+                        if (!(b.flags & BJ_COMPARE) || W.first + W.count > items[W.job] || W.first + W.count < W.first)
+                            return fail(c, KC_EINVAL, "work %d: comparison range outside job %u", w, W.job);
+                    } else {
+                        return fail(c, KC_EINVAL, "work %d: kind %u", w, W.kind);
+                    }
+                    add(W.job, W.kind == KC_WORK_DIGEST ? 0u : 1u, W.first, W.count);
+                }
+            }
+            uint64_t it = 0;
+            for (auto &r : rg) {
+                r.item_first = it;
+                it += r.kind == 0 ? (r.count + 7) / 8 : r.count;
+            }
+            tb.items = it;
+            tb.nranges = (int)rg.size();
+            tb.n = njobs;
+            put(parts[TP_JOBS], bj);
+            put(parts[TP_WORK], rg);
+            return KC_OK;
+        },
+        &t);
+    if (s != KC_OK) return s;
+    // digest shape: the persistent grid fills the GPU; warps take digest
+    // items and comparison items alike
+    DigestShape shape = pick_shape(c, page_bytes, t->items * 8);
+    shape.lanes = 1;
+    shape.ctas = (int)std::min<uint64_t>((uint64_t)shape.ctas, std::max<uint64_t>(1, t->items));
+    KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
+    {
+        Trace tr(c, st);
+        KC_CHECK(c, launch_batch(t->jobs(), njobs, t->work(), t->nranges, t->items, page_bytes, shape, atol, rtol,
+                                 task_counter(c), c->sms, st),
+                 "batch launch");
+    }
+    touch(c, t, st);
+    return t->any_lost ? fail(c, KC_EBUF, "one or more jobs were marked lost") : KC_OK;
 }
 
 }  // extern "C"

@@ -32,12 +32,28 @@ ESIZE = {U8: 1, RAW: 1, I32: 4, F16: 2, BF16: 2, F32: 4}
 EXPORTS = ["kc_version", "kc_launch_count", "kc_status_name", "kc_last_error", "kc_create", "kc_destroy", "kc_sync",
            "kc_buf_status", "kc_set_digest_shape", "kc_set_trace_events", "kc_get_digest_shape", "kc_page_count",
            "kc_digest", "kc_census", "kc_scan", "kc_dedup", "kc_restore", "kc_compare",
-           "kc_census_static"]
+           "kc_census_static", "kc_batch_run"]
 
 
 class KcBuf(ctypes.Structure):
     _fields_ = [("base_va", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
                 ("dtype", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+JOB_DIGEST, JOB_COMPARE, JOB_INIT = 0x10, 0x20, 0x40
+WORK_DIGEST, WORK_COMPARE = 0, 1
+BATCH_ITEM_BYTES = 65536
+
+
+class KcJob(ctypes.Structure):
+    _fields_ = [("got_va", ctypes.c_uint64), ("want_va", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
+                ("dtype", ctypes.c_int32), ("flags", ctypes.c_int32), ("d_hash", ctypes.c_uint64),
+                ("d_zero", ctypes.c_uint64), ("d_cmp", ctypes.c_uint64), ("reserved", ctypes.c_uint64)]
+
+
+class KcWork(ctypes.Structure):
+    _fields_ = [("job", ctypes.c_uint32), ("kind", ctypes.c_uint32), ("first", ctypes.c_uint64),
+                ("count", ctypes.c_uint64)]
 
 
 class KcError(RuntimeError):
@@ -93,6 +109,9 @@ def load(build_if_missing: bool = False):
     L.kc_digest.argtypes = [vp, B, i32, u32, vp, vp, vp, vp]
     L.kc_census.restype = st
     L.kc_census.argtypes = [vp, B, i32, u64, u64, vp, u64, vp, vp]
+    L.kc_batch_run.restype = st
+    L.kc_batch_run.argtypes = [vp, ctypes.POINTER(KcJob), i32, u32, ctypes.c_double, ctypes.c_double,
+                               ctypes.POINTER(KcWork), i32, vp]
     L.kc_census_static.restype = st
     L.kc_census_static.argtypes = [B, i32, u64, u64, vp, u64, vp, vp]
     L.kc_scan.restype = st
@@ -238,12 +257,39 @@ class Context:
                                                n_pages, _ptr(arena), arena_bytes,
                                                _stream(stream)), allow)
 
+    def batch_run(self, job_array, page_bytes, atol=0.0, rtol=0.0, work_array=None, stream=None,
+                  allow=(OK, EBUF)):
+        j = job_array if isinstance(job_array, ctypes.Array) else jobs(job_array)
+        w = work_array
+        if w is not None and not isinstance(w, ctypes.Array):
+            w = work(w)
+        return self._check(self.lib.kc_batch_run(self.h, j, len(j), page_bytes, float(atol), float(rtol), w,
+                                                 0 if w is None else len(w), _stream(stream)), allow)
+
     def compare(self, got, want, atol, rtol, out, stream=None, allow=(OK, EBUF)):
         g = got if isinstance(got, ctypes.Array) else bufs(got)
         w = want if isinstance(want, ctypes.Array) else bufs(want)
         assert len(g) == len(w)
         return self._check(self.lib.kc_compare(self.h, g, w, len(g), float(atol), float(rtol),
                                                _ptr(out), _stream(stream)), allow)
+
+
+def jobs(items) -> ctypes.Array:
+    """Array of kc_job from dicts with keys got, want, bytes, dtype, flags,
+    hash, zero, cmp (tensors or integer addresses; absent = 0)."""
+    arr = (KcJob * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = KcJob(_ptr(it.get("got")), _ptr(it.get("want")), int(it["bytes"]), int(it.get("dtype", RAW)),
+                       int(it["flags"]), _ptr(it.get("hash")), _ptr(it.get("zero")), _ptr(it.get("cmp")), 0)
+    return arr
+
+
+def work(items) -> ctypes.Array:
+    """Array of kc_work from (job, kind, first, count) tuples."""
+    arr = (KcWork * len(items))()
+    for i, (j, k, f, c) in enumerate(items):
+        arr[i] = KcWork(int(j), int(k), int(f), int(c))
+    return arr
 
 
 def census_static(regions, win_lo, win_hi, hits_out, cap, counts_out, stream=None) -> int:

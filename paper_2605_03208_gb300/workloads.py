@@ -401,3 +401,82 @@ def moe_pairs(seed: int = 0, rows: int = 4096, cols: int = 7168, device: str = "
     torch.cuda.synchronize()
     return [(want2.clone(), want2, dict(perturbed=np.zeros(0, np.int64))),
             (got, want, dict(perturbed=idx))]
+
+
+# --------------------------------------------------------------------------
+# Batched validation jobs: many (got, want) pairs of uneven sizes
+# --------------------------------------------------------------------------
+
+@dataclass
+class JobSet:
+    """Jobs laid out in two device buffers (got, want) at 256-byte offsets."""
+    sizes: list
+    dtypes: list
+    offsets: list
+    got: object = None       # torch uint8 tensor
+    want: object = None
+    truth: dict = field(default_factory=dict)
+
+    @property
+    def total_bytes(self) -> int:
+        return int(sum(self.sizes))
+
+
+def batch_jobs(seed: int = 0, n: int = 4096, lo: int = 256, hi: int = 64 * MiB,
+               frac_bad: float = 0.05, device: str = "cuda") -> JobSet:
+    """n jobs, sizes log-uniform in [lo, hi], dtypes uniform over fp32 / fp16 /
+    bf16 / int32 / uint8; want holds finite values of the dtype, got is a copy
+    with 1..64 planted mismatches in a `frac_bad` share of the jobs (one ulp
+    step of the bit pattern for floats, +1 for integers)."""
+    import torch
+    rng = np.random.default_rng(seed + 606)
+    dts = [DT_F32, DT_F16, DT_BF16, DT_I32, DT_U8]
+    sizes, dtypes, offsets = [], [], []
+    off = 0
+    for _ in range(n):
+        dt = dts[int(rng.integers(0, 5))]
+        b = int(np.exp(rng.uniform(math.log(lo), math.log(hi))))
+        b = max(16, b // 16 * 16)
+        sizes.append(b)
+        dtypes.append(dt)
+        offsets.append(off)
+        off += (b + 255) // 256 * 256
+    total = off
+    want = torch.empty(total, dtype=torch.uint8, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed + 607)
+    for b, dt, o in zip(sizes, dtypes, offsets):
+        seg = want[o:o + b]
+        if dt == DT_F32:
+            seg.view(torch.float32).copy_(torch.randn(b // 4, generator=g, device=device))
+        elif dt == DT_F16:
+            seg.view(torch.float16).copy_(torch.randn(b // 2, generator=g, device=device))
+        elif dt == DT_BF16:
+            seg.view(torch.bfloat16).copy_(torch.randn(b // 2, generator=g, device=device))
+        elif dt == DT_I32:
+            seg.view(torch.int32).copy_(torch.randint(-2**31, 2**31 - 1, (b // 4,), generator=g,
+                                                      device=device, dtype=torch.int64).to(torch.int32))
+        else:
+            seg.copy_(torch.randint(0, 256, (b,), generator=g, device=device, dtype=torch.int32)
+                      .to(torch.uint8))
+    got = want.clone()
+    bad = {}
+    for k in np.nonzero(rng.random(n) < frac_bad)[0].tolist():
+        dt, b, o = dtypes[k], sizes[k], offsets[k]
+        es = ESIZE[dt]
+        ne = b // es
+        m = int(min(ne, rng.integers(1, 65)))
+        idx = np.sort(rng.choice(ne, m, replace=False))
+        ti = torch.from_numpy(idx).to(device)
+        if dt in (DT_F32, DT_I32):
+            v = got[o:o + b].view(torch.int32)
+            v[ti] = v[ti] + 1 if dt == DT_I32 else v[ti] ^ 1
+        elif dt in (DT_F16, DT_BF16):
+            v = got[o:o + b].view(torch.int16)
+            v[ti] = v[ti] ^ 1
+        else:
+            v = got[o:o + b]
+            v[ti] = v[ti] + 1
+        bad[k] = idx
+    torch.cuda.synchronize()
+    return JobSet(sizes, dtypes, offsets, got, want, dict(planted=bad))
