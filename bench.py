@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--variant", default="full", choices=["full", "152MB"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
+    ap.add_argument("--batched-jobs", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -159,26 +161,36 @@ class KcStep:
         self.N = sum(int(s) for s in snap.sizes)
         self.C = sum(x.numel() for x in self.g)
 
-    def run(self, stream, trace=None):
-        """Enqueue one step.  trace: dict op -> (start, stop) events for main kernels."""
+    def run(self, stream, ev=None):
+        """Enqueue one step.  ev: optional dict of (start, stop) torch events:
+        keys scan / dedup / restore / compare are recorded around the whole
+        call (every kernel of it); key digest_kernel is handed to the library,
+        which records it around the digest kernel alone."""
         ctx, S = self.ctx, self.S
-        t = trace or {}
-        if "scan" in t:
-            ctx.set_trace_events(*t["scan"])
+        e = ev or {}
+
+        def mark(op, i):
+            if op in e:
+                e[op][i].record(stream)
+
+        if "digest_kernel" in e:
+            ctx.set_trace_events(*e["digest_kernel"])
+        mark("scan", 0)
         ctx.scan(self.b, S, self.hash, self.zero, self.pf, self.win[0], self.win[1], self.hits,
                  self.cap, self.counts, stream)
-        if "dedup" in t:
-            ctx.set_trace_events(*t["dedup"])
+        mark("scan", 1)
+        if "digest_kernel" in e:
+            ctx.set_trace_events(None, None)
+        mark("dedup", 0)
         ctx.dedup(self.b, S, self.hash, self.zero, self.table, self.arena, self.P * S, self.nblobs,
                   stream)
-        if "restore" in t:
-            ctx.set_trace_events(*t["restore"])
+        mark("dedup", 1)
+        mark("restore", 0)
         ctx.restore(self.b, S, self.table, self.P, self.arena, self.P * S, stream)
-        if "compare" in t:
-            ctx.set_trace_events(*t["compare"])
+        mark("restore", 1)
+        mark("compare", 0)
         ctx.compare(self.gb, self.wb, 0.0, 0.0, self.cmp, stream)
-        if t:
-            ctx.set_trace_events(None, None)
+        mark("compare", 1)
 
     def unique_bytes(self):
         nb = int(self.nblobs.cpu().numpy().view(np.uint64)[0])
@@ -194,6 +206,29 @@ class KcStep:
             seen.add(b)
             lens.append(min(self.S, int(sizes[int(row["alloc_id"])]) - int(row["va_offset"])))
         return nb, int(sum(lens))
+
+
+# DRAM traffic of one digest_kernel<census> launch on this workload, from the
+# ncu capture summarised in profiles/digest_kernel_llama400.md, valid only for
+# the kernel sources it was taken on (sha1 of each file, first 8 hex digits).
+DIGEST_TRAFFIC = {"bytes": 402_742_016 + 3_481_088,
+                  "sources": {"k_digest.cu": "eac3c08b", "digest_task.cuh": "e56d6bfd",
+                              "kc_device.cuh": "8385f4d8"}}
+
+
+def digest_traffic():
+    """DRAM bytes per digest launch measured by ncu, or None once any of the
+    kernel's sources differs from the ones the capture was taken on."""
+    import hashlib
+    for f, want in DIGEST_TRAFFIC["sources"].items():
+        path = os.path.join(ROOT, "paper_2605_03208_gb300", "csrc", f)
+        try:
+            with open(path, "rb") as fh:
+                if hashlib.sha1(fh.read()).hexdigest()[:8] != want:
+                    return None
+        except OSError:
+            return None
+    return DIGEST_TRAFFIC["bytes"]
 
 
 def algorithmic_bytes(N, U, C, P, pairs):
@@ -312,8 +347,8 @@ def run_kc(args):
     # ---- timed region: exactly K steps, device time with CUDA events
     ops = ["scan", "dedup", "restore", "compare"]
     tr = {op: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)] for op in ops}
-    for op in ops:          # torch creates the cudaEvent_t on first record
+               for _ in range(args.steps)] for op in ops + ["digest_kernel"]}
+    for op in tr:           # torch creates the cudaEvent_t on first record
         for a, b in tr[op]:
             a.record(stream)
             b.record(stream)
@@ -323,7 +358,7 @@ def run_kc(args):
     t_wall0 = time.time()
     e0.record(stream)
     for i in range(args.steps):
-        step.run(stream, {op: tr[op][i] for op in ops})
+        step.run(stream, {op: tr[op][i] for op in tr})
     e1.record(stream)
     barrier()
     t_wall1 = time.time()
@@ -334,7 +369,7 @@ def run_kc(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
     ms = ms_total / args.steps
-    op_ms = {op: statistics.mean(a.elapsed_time(b) for a, b in tr[op]) for op in ops}
+    op_ms = {op: statistics.mean(a.elapsed_time(b) for a, b in tr[op]) for op in tr}
     time.sleep(0.3)
     sampler.stop()
     st = ctx.sync(stream)
@@ -372,7 +407,7 @@ def run_kc(args):
     peak, peak_kind = peaks()
     value = world * step_bytes / (ms / 1000) / 1e9
     scan_bytes = ab["scan"]
-    achieved = scan_bytes / (op_ms["scan"] / 1000) / 1e9
+    achieved = scan_bytes / (op_ms["digest_kernel"] / 1000) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -385,16 +420,21 @@ def run_kc(args):
         "hbm_frac": value / world / peak,
         "roofline": {"bound": "hbm", "kernel": "digest_kernel<census> (kc_scan)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                     "algorithmic_bytes": scan_bytes},
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": digest_traffic(), "algorithmic_bytes": scan_bytes,
+                     "kernel_ms": op_ms["digest_kernel"]},
         "ops": {op: {"ms": op_ms[op], "GB/s": ab[op] / (op_ms[op] / 1000) / 1e9,
                      "frac": ab[op] / (op_ms[op] / 1000) / 1e9 / peak,
                      "algorithmic_bytes": ab[op]} for op in ops},
+        "ops_timing": "CUDA events around each whole call (all of its kernels); the roofline "
+                      "kernel is timed by events the library records around it alone",
         "e2e": {"value": world * step_bytes / (e2e_ms / 1000) / 1e9, "unit": "GB/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": sampler.summary(t_wall0, t_wall1),
     }
+    if not args.no_batched:
+        line["batched"] = run_batched_section(args, device, peak)
     if rank == 0 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
         sample = list(range(len(snap.sizes)))
@@ -412,6 +452,84 @@ def run_kc(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched_section(args, device, peak):
+    """Batched form vs plain form on 4096 validation jobs (log-uniform
+    256 B - 64 MiB, five dtypes, 5% with planted mismatches): autotuned
+    page size and CTA shape, one graph-captured kc_batch_run per step,
+    against one kc_digest + one kc_compare call per job at the same page
+    size.  Both forms' outputs are checked for byte equality."""
+    import torch
+    from paper_2605_03208_gb300 import batch as B
+    from paper_2605_03208_gb300 import kc
+    from paper_2605_03208_gb300 import workloads as W
+
+    t0 = time.time()
+    js = W.batch_jobs(args.seed, n=args.batched_jobs, lo=256, hi=64 * W.MiB, frac_bad=0.05, device=device)
+    t_gen = time.time() - t0
+    ctx_b, ctx_p = kc.Context(torch.cuda.current_device()), kc.Context(torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    tune = B.autotune(ctx_b, js, budget_s=90.0)
+    t_tune = time.time() - t0
+    S = tune["page_bytes"]
+    pb, pp = B.make_plan(js, S), B.make_plan(js, S)
+    # batched: captured once, replayed
+    for _ in range(3):
+        B.run_batched(ctx_b, pb, stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        B.run_batched(ctx_b, pb, stream=torch.cuda.current_stream())
+    K = 10
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / K
+    # plain: one call per buffer per op, same page size, default shapes
+    B.run_plain(ctx_p, pp, stream=stream)
+    torch.cuda.synchronize()
+    Kp = 3
+    l1 = kc.launch_count()
+    e0.record(stream)
+    for _ in range(Kp):
+        B.run_plain(ctx_p, pp, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_launches = (kc.launch_count() - l1) // Kp
+    ms_p = e0.elapsed_time(e1) / Kp
+    equal = B.same_results(pb, pp)
+    _, _, rec = B.results(pb)
+    found = sum(1 for k, idx in js.truth["planted"].items()
+                if rec[k]["mismatches"] == len(idx) and rec[k]["first"] == idx[0])
+    clean = sum(1 for k in range(len(js.sizes)) if k not in js.truth["planted"] and rec[k]["mismatches"] == 0)
+    ab = B.algorithmic_bytes(pb)
+    gbs = ab / (ms_b / 1000) / 1e9
+    out = {
+        "workload": f"{len(js.sizes)} jobs, log-uniform 256 B-64 MiB, dtypes fp32/fp16/bf16/int32/uint8, "
+                    "5% planted mismatches; digest(got) + compare(got, want)",
+        "job_bytes": js.total_bytes, "pages": pb.total_pages, "page_bytes": S,
+        "shape": {k: tune[k] for k in ("warps", "stages", "chunk")}, "autotune_cached": tune["cached"],
+        "autotune_s": round(t_tune, 2), "autotune_swept": tune.get("swept"), "gen_s": round(t_gen, 2),
+        "algorithmic_bytes": ab, "batched_ms": ms_b, "plain_ms": ms_p, "speedup": ms_p / ms_b,
+        "GB/s": gbs, "frac": gbs / peak, "plain_GB/s": ab / (ms_p / 1000) / 1e9,
+        "launches_per_step": {"batched": 2, "plain": plain_launches},
+        "bit_equal_batched_vs_plain": bool(equal),
+        "planted_found": f"{found}/{len(js.truth['planted'])}", "clean_jobs_clean": clean,
+        "timing": f"graph replay x{K} (batched), {Kp} passes (plain); inputs {js.total_bytes * 2 / 2**30:.1f} GiB > L2",
+    }
+    ctx_b.close()
+    ctx_p.close()
+    del pb, pp, js, g
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():

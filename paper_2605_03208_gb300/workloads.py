@@ -466,7 +466,7 @@ def batch_jobs(seed: int = 0, n: int = 4096, lo: int = 256, hi: int = 64 * MiB,
         es = ESIZE[dt]
         ne = b // es
         m = int(min(ne, rng.integers(1, 65)))
-        idx = np.sort(rng.choice(ne, m, replace=False))
+        idx = np.unique(rng.integers(0, ne, m))   # sorted; duplicates dropped, so len(idx) <= m
         ti = torch.from_numpy(idx).to(device)
         if dt in (DT_F32, DT_I32):
             v = got[o:o + b].view(torch.int32)
