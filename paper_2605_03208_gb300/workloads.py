@@ -446,37 +446,70 @@ def batch_jobs(seed: int = 0, n: int = 4096, lo: int = 256, hi: int = 64 * MiB,
     g = torch.Generator(device=device)
     g.manual_seed(seed + 607)
     for b, dt, o in zip(sizes, dtypes, offsets):
-        seg = want[o:o + b]
-        if dt == DT_F32:
-            seg.view(torch.float32).copy_(torch.randn(b // 4, generator=g, device=device))
-        elif dt == DT_F16:
-            seg.view(torch.float16).copy_(torch.randn(b // 2, generator=g, device=device))
-        elif dt == DT_BF16:
-            seg.view(torch.bfloat16).copy_(torch.randn(b // 2, generator=g, device=device))
-        elif dt == DT_I32:
-            seg.view(torch.int32).copy_(torch.randint(-2**31, 2**31 - 1, (b // 4,), generator=g,
-                                                      device=device, dtype=torch.int64).to(torch.int32))
-        else:
-            seg.copy_(torch.randint(0, 256, (b,), generator=g, device=device, dtype=torch.int32)
-                      .to(torch.uint8))
+        fill_typed(want[o:o + b], dt, g)
     got = want.clone()
     bad = {}
     for k in np.nonzero(rng.random(n) < frac_bad)[0].tolist():
         dt, b, o = dtypes[k], sizes[k], offsets[k]
-        es = ESIZE[dt]
-        ne = b // es
-        m = int(min(ne, rng.integers(1, 65)))
-        idx = np.unique(rng.integers(0, ne, m))   # sorted; duplicates dropped, so len(idx) <= m
-        ti = torch.from_numpy(idx).to(device)
-        if dt in (DT_F32, DT_I32):
-            v = got[o:o + b].view(torch.int32)
-            v[ti] = v[ti] + 1 if dt == DT_I32 else v[ti] ^ 1
-        elif dt in (DT_F16, DT_BF16):
-            v = got[o:o + b].view(torch.int16)
-            v[ti] = v[ti] ^ 1
-        else:
-            v = got[o:o + b]
-            v[ti] = v[ti] + 1
-        bad[k] = idx
+        m = int(rng.integers(1, 65))
+        bad[k] = plant(got[o:o + b], dt, m, rng)
     torch.cuda.synchronize()
     return JobSet(sizes, dtypes, offsets, got, want, dict(planted=bad))
+
+
+def fill_typed(seg, dt: int, g) -> None:
+    """Fill a device byte segment with finite values of dtype dt: N(0, 1)
+    for the float types, uniform 32-bit integers, uniform bytes."""
+    import torch
+    b = seg.numel()
+    dev = seg.device
+    if dt == DT_F32:
+        seg.view(torch.float32).copy_(torch.randn(b // 4, generator=g, device=dev))
+    elif dt == DT_F16:
+        seg.view(torch.float16).copy_(torch.randn(b // 2, generator=g, device=dev))
+    elif dt == DT_BF16:
+        seg.view(torch.bfloat16).copy_(torch.randn(b // 2, generator=g, device=dev))
+    elif dt == DT_I32:
+        seg.view(torch.int32).copy_(torch.randint(-2**31, 2**31 - 1, (b // 4,), generator=g, device=dev,
+                                                  dtype=torch.int64).to(torch.int32))
+    else:
+        seg.copy_(torch.randint(0, 256, (b,), generator=g, device=dev, dtype=torch.int32).to(torch.uint8))
+
+
+def plant(seg, dt: int, m: int, rng) -> np.ndarray:
+    """Change up to m elements of a device byte segment in place (drawn
+    with replacement, duplicates dropped): the lowest bit of a float's
+    pattern flipped (one ulp), +1 for integers.  Returns the sorted element
+    indices changed."""
+    import torch
+    ne = seg.numel() // ESIZE[dt]
+    idx = np.unique(rng.integers(0, ne, int(min(m, ne))))
+    ti = torch.from_numpy(idx).to(seg.device)
+    if dt in (DT_F32, DT_I32):
+        v = seg.view(torch.int32)
+        v[ti] = v[ti] + 1 if dt == DT_I32 else v[ti] ^ 1
+    elif dt in (DT_F16, DT_BF16):
+        v = seg.view(torch.int16)
+        v[ti] = v[ti] ^ 1
+    else:
+        seg[ti] = seg[ti] + 1
+    return idx
+
+
+def golden_set(seed: int = 0, n: int = 64, lo: int = MiB, hi: int = 2 * GiB, device: str = "cuda"):
+    """n resident golden buffers, sizes log-uniform in [lo, hi] (multiples
+    of 256 bytes), dtypes uniform over the five, in one device allocation.
+    Returns (data u8 tensor, sizes, dtypes, offsets)."""
+    import torch
+    rng = np.random.default_rng(seed + 808)
+    dts = [DT_F32, DT_F16, DT_BF16, DT_I32, DT_U8]
+    sizes = [int(np.exp(rng.uniform(math.log(lo), math.log(hi)))) // 256 * 256 for _ in range(n)]
+    dtypes = [dts[int(rng.integers(0, 5))] for _ in range(n)]
+    offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64).tolist()
+    data = torch.empty(int(sum(sizes)), dtype=torch.uint8, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed + 809)
+    for b, dt, o in zip(sizes, dtypes, offsets):
+        fill_typed(data[o:o + b], dt, g)
+    torch.cuda.synchronize()
+    return data, sizes, dtypes, offsets

@@ -42,8 +42,10 @@ def test_batched_4096_jobs_equal_plain_and_oracle(jobset, tmp_path):
         g = torch.cuda.CUDAGraph()
         pb.hash.fill_(-1)
         pb.cmp.fill_(0xEE)
-        with torch.cuda.graph(g, stream=s):
-            assert B.run_batched(ctx_b, pb, stream=torch.cuda.current_stream()) == kc.OK
+        cs = torch.cuda.Stream()
+        cs.wait_stream(s)
+        with torch.cuda.graph(g, stream=cs):
+            assert B.run_batched(ctx_b, pb, stream=cs) == kc.OK
         g.replay()
         assert B.run_plain(ctx_p, pp, stream=s) == kc.OK
         torch.cuda.synchronize()
