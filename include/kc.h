@@ -316,6 +316,16 @@ KC_API kc_status kc_compare(kc_ctx *ctx, const kc_buf *got, const kc_buf *want, 
  * with order-independent merges, so the result does not depend on how the
  * work was split.  Without `work`, every compare job is initialised.
  *
+ * Completion signal (optional, per job): with d_done set, the launch
+ * stores 1 to *d_done once every unit of the job in this launch has
+ * finished and its outputs are visible to the host (system-scope fence);
+ * a job with no unit in the launch is flagged when the launch starts.  With
+ * d_cmp_copy also set, the job's comparison record (accumulated over every
+ * launch so far) is copied there just before the flag.  Both may point to
+ * pinned host memory the device can address, so that a host loop sees a
+ * job finish while the rest of the launch is still running.  The caller
+ * clears *d_done before the launch; the launch only sets it.
+ *
  * Repeated calls with the same jobs and work hit the context's table cache
  * and can be captured in a CUDA graph.  The digest kernel shape
  * (kc_set_digest_shape) also applies here.
@@ -337,8 +347,9 @@ typedef struct {
     uint64_t *d_hash;      /* KC_JOB_DIGEST: page hashes */
     uint8_t *d_zero;       /* KC_JOB_DIGEST: page zero flags */
     kc_cmp_result *d_cmp;  /* KC_JOB_COMPARE: the comparison record */
-    uint64_t reserved;
-} kc_job;
+    uint32_t *d_done;      /* optional completion flag (see above), or NULL */
+    kc_cmp_result *d_cmp_copy; /* optional copy of the finished record, or NULL */
+} kc_job;                  /* 72 bytes */
 
 typedef struct {
     uint32_t job;          /* index in the job list */
@@ -349,6 +360,15 @@ typedef struct {
 
 KC_API kc_status kc_batch_run(kc_ctx *ctx, const kc_job *jobs, int njobs, uint32_t page_bytes, double atol,
                               double rtol, const kc_work *work, int nwork, void *stream);
+
+/* Host helper for the completion flags above (no device work): reads the
+ * n flags at `flags` (host memory the device writes, e.g. pinned), writes
+ * the indices of those that are non-zero to idx_out (room for n) and
+ * returns their number.  The reads are followed by an acquire fence, so
+ * the caller's later reads of a flagged job's outputs see what the device
+ * wrote before setting the flag, also on weakly ordered hosts.  Returns -1
+ * if flags or idx_out is NULL or n < 0. */
+KC_API int kc_poll_flags(const uint32_t *flags, int n, int32_t *idx_out);
 
 #ifdef __cplusplus
 }

@@ -131,8 +131,10 @@ __device__ __forceinline__ void cmp_vec(uint4 g, uint4 w, unsigned long long fir
     cmp_word<DT>(g.w, w.w, first_elem + 3 * per, atol, rtol, acc);
 }
 
-// One tile of one pair, shared by `nthr` threads (tid = 0 .. nthr-1).
-template <int DT>
+// One tile of one pair, shared by `nthr` threads (tid = 0 .. nthr-1); each
+// thread keeps U 16-byte loads of each buffer in flight (a CTA-wide tile
+// needs few, a warp alone on a tile needs more to cover the DRAM latency).
+template <int DT, int U>
 __device__ void cmp_tile(const CmpPair &pr, uint64_t tile_in_pair, double atol, double rtol, CmpAcc &acc,
                          uint32_t tid, uint32_t nthr) {
     constexpr int ES = esize<DT>();
@@ -143,15 +145,15 @@ __device__ void cmp_tile(const CmpPair &pr, uint64_t tile_in_pair, double atol, 
     const uint8_t *w = reinterpret_cast<const uint8_t *>(pr.want) + t0;
     const uint64_t nvec = tlen >> 4;
     uint64_t v = tid;
-    for (; v + 3 * nthr < nvec; v += 4 * nthr) {
-        uint4 gv[4], wv[4];
+    for (; v + (U - 1) * nthr < nvec; v += U * nthr) {
+        uint4 gv[U], wv[U];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < U; ++j) {
             gv[j] = ldg_stream(g + 16 * (v + j * nthr));
             wv[j] = ldg_stream(w + 16 * (v + j * nthr));
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < U; ++j)
             cmp_vec<DT>(gv[j], wv[j], (t0 + 16 * (v + j * nthr)) / ES, atol, rtol, acc);
     }
     for (; v < nvec; v += nthr) {
@@ -208,14 +210,15 @@ __device__ __forceinline__ void cmp_warp_flush(const CmpAcc &acc, kc_cmp_result 
 }
 
 // Comparison of one tile by `nthr` threads, dispatched on the pair's dtype.
+template <int U>
 __device__ __forceinline__ void cmp_tile_any(const CmpPair &pr, uint64_t tile, double atol, double rtol, CmpAcc &acc,
                                              uint32_t tid, uint32_t nthr) {
     switch (pr.dtype) {
-    case KC_F32: cmp_tile<KC_F32>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    case KC_F16: cmp_tile<KC_F16>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    case KC_BF16: cmp_tile<KC_BF16>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    case KC_I32: cmp_tile<KC_I32>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    default: cmp_tile<KC_U8>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_F32: cmp_tile<KC_F32, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_F16: cmp_tile<KC_F16, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_BF16: cmp_tile<KC_BF16, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_I32: cmp_tile<KC_I32, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    default: cmp_tile<KC_U8, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
     }
 }
 

@@ -23,15 +23,44 @@ namespace kc {
 
 constexpr int BATCH_PPW = 8;   // pages per digest item (one XXH64 lane per thread)
 
-__global__ void batch_init_kernel(const BatchJob *__restrict__ jobs, int njobs) {
+// Per launch: comparison records of jobs that start here, the per-job
+// count of unfinished items, and the completion flag of jobs with no item.
+__global__ void batch_init_kernel(const BatchJob *__restrict__ jobs, int njobs, uint32_t *__restrict__ left) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= njobs) return;
     const BatchJob J = jobs[i];
     if ((J.flags & BJ_COMPARE) && (J.flags & BJ_INIT)) cmp_record_init(J.cmp, (J.flags & BJ_LOST) ? KC_EBUF : KC_OK);
+    left[i] = J.items;
+    if (J.done && J.items == 0) {
+        if (J.cmp_copy && (J.flags & BJ_COMPARE)) *J.cmp_copy = *J.cmp;
+        __threadfence_system();
+        *reinterpret_cast<volatile uint32_t *>(J.done) = 1u;
+    }
+}
+
+// Called by every lane of a warp after it finished one item of job J.  The
+// warp's outputs are fenced at system scope before the job's count drops;
+// the warp that takes it to zero copies the record (if asked) and sets the
+// flag, so a host that sees the flag sees every output of the job.
+__device__ __forceinline__ void batch_item_done(const BatchJob &J, uint32_t *left) {
+    __threadfence_system();
+    __syncwarp();
+    if (lane_id() != 0) return;
+    if (atomicSub(left, 1u) != 1u) return;
+    __threadfence_system();
+    if (J.cmp_copy && (J.flags & BJ_COMPARE)) {
+        const volatile unsigned long long *from = reinterpret_cast<const volatile unsigned long long *>(J.cmp);
+        volatile unsigned long long *to = reinterpret_cast<volatile unsigned long long *>(J.cmp_copy);
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(kc_cmp_result) / 8); ++k) to[k] = from[k];
+    }
+    __threadfence_system();
+    *reinterpret_cast<volatile uint32_t *>(J.done) = 1u;
 }
 
 template <int CHUNK>
 __global__ void __launch_bounds__(512) batch_kernel(const BatchJob *__restrict__ jobs,
+                                                    uint32_t *__restrict__ left,
                                                     const BatchRange *__restrict__ ranges, int nranges,
                                                     uint64_t nitems, uint32_t page, uint32_t log2page, int stages,
                                                     int chunk, double atol, double rtol, uint32_t *__restrict__ ctr) {
@@ -80,9 +109,10 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchJob *__restrict__
             const uint64_t tiles = (J.bytes + CMP_TILE_BYTES - 1) / CMP_TILE_BYTES;
             const uint64_t t0 = (R.first + k) * (BATCH_CMP_ITEM_BYTES / CMP_TILE_BYTES);
             for (uint64_t tile = t0; tile < t0 + BATCH_CMP_ITEM_BYTES / CMP_TILE_BYTES && tile < tiles; ++tile)
-                cmp_tile_any(pr, tile, atol, rtol, acc, lane, 32);
+                cmp_tile_any<6>(pr, tile, atol, rtol, acc, lane, 32);
             cmp_warp_flush(acc, J.cmp);
         }
+        if (J.done) batch_item_done(J, left + R.job);
     }
 }
 
@@ -98,10 +128,10 @@ cudaError_t setup_batch_kernels() {
     return setup_batch_one<1024>();
 }
 
-cudaError_t launch_batch(const BatchJob *jobs, int njobs, const BatchRange *ranges, int nranges, uint64_t nitems,
-                         uint32_t page, const DigestShape &shape, double atol, double rtol, uint32_t *ctr, int sms,
-                         cudaStream_t st) {
-    batch_init_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(jobs, njobs);
+cudaError_t launch_batch(const BatchJob *jobs, int njobs, uint32_t *left, const BatchRange *ranges, int nranges,
+                         uint64_t nitems, uint32_t page, const DigestShape &shape, double atol, double rtol,
+                         uint32_t *ctr, int sms, cudaStream_t st) {
+    batch_init_kernel<<<(njobs + 255) / 256, 256, 0, st>>>(jobs, njobs, left);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || nitems == 0) return e;
@@ -111,16 +141,16 @@ cudaError_t launch_batch(const BatchJob *jobs, int njobs, const BatchRange *rang
     const dim3 grid(shape.ctas), block(32 * shape.warps);
     switch (shape.chunk) {
     case 512:
-        batch_kernel<512><<<grid, block, smem, st>>>(jobs, ranges, nranges, nitems, page, log2page, shape.stages,
-                                                     shape.chunk, atol, rtol, ctr);
+        batch_kernel<512><<<grid, block, smem, st>>>(jobs, left, ranges, nranges, nitems, page, log2page,
+                                                     shape.stages, shape.chunk, atol, rtol, ctr);
         break;
     case 1024:
-        batch_kernel<1024><<<grid, block, smem, st>>>(jobs, ranges, nranges, nitems, page, log2page, shape.stages,
-                                                      shape.chunk, atol, rtol, ctr);
+        batch_kernel<1024><<<grid, block, smem, st>>>(jobs, left, ranges, nranges, nitems, page, log2page,
+                                                      shape.stages, shape.chunk, atol, rtol, ctr);
         break;
     default:
-        batch_kernel<0><<<grid, block, smem, st>>>(jobs, ranges, nranges, nitems, page, log2page, shape.stages,
-                                                   shape.chunk, atol, rtol, ctr);
+        batch_kernel<0><<<grid, block, smem, st>>>(jobs, left, ranges, nranges, nitems, page, log2page,
+                                                   shape.stages, shape.chunk, atol, rtol, ctr);
     }
     count_launches(1);
     (void)sms;

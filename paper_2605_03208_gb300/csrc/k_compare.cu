@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(CMP_THREADS) cmp_kernel(const CmpPair *__restr
         }
         if (moved) pr = pairs[k];
         if (pr.lost) continue;
-        cmp_tile_any(pr, tile - pr.tile_first, atol, rtol, acc, threadIdx.x, CMP_THREADS);
+        cmp_tile_any<4>(pr, tile - pr.tile_first, atol, rtol, acc, threadIdx.x, CMP_THREADS);
     }
     cmp_flush(acc, &out[k], red);
 }

@@ -20,6 +20,8 @@
 //   5. blob ids = exclusive scan of "page is canonical" in page order; the
 //      page table is written VA-faithfully (region index, offset);
 //   6. pack copies every canonical page into its arena slot, zero-filled.
+// Snapshots of at most DD_SMALL pages replace steps 1-5 by a hash table in
+// one CTA's shared memory (no sort; see "small snapshots" below).
 #include <cuda_runtime.h>
 
 #include "kc_device.cuh"
@@ -30,8 +32,6 @@ namespace kc {
 constexpr int RS_TILE_THREADS = 256;
 constexpr int RS_TILE_ITEMS = 16;
 constexpr int RS_TILE = RS_TILE_THREADS * RS_TILE_ITEMS;      // 4096 keys per tile
-constexpr int RS_SMALL_THREADS = 512;
-constexpr int RS_SMALL = RS_SMALL_THREADS * RS_TILE_ITEMS;    // 8192 keys, one CTA
 constexpr uint32_t DD_PIECE = 16 * 1024;
 constexpr int SORT_BITS = 32;   // bits of the hash the radix sort orders by
 
@@ -254,145 +254,6 @@ __device__ __forceinline__ uint32_t block_excl_max(uint32_t v, uint32_t *ws) {
     return prev;
 }
 
-// ---- small snapshots (P <= RS_SMALL pages): the whole front in one CTA -----
-//
-// Compaction of the non-zero pages, the radix passes and the segment
-// scan run in one CTA of 512 threads.  Registers hold the current order
-// (warp-striped: warp w, round r, lane j holds element 512 w + 32 r + j);
-// shared memory receives each pass's stable scatter.
-__global__ void __launch_bounds__(RS_SMALL_THREADS) dd_small_front_kernel(
-    const uint64_t *__restrict__ hash, const uint8_t *__restrict__ zero, uint32_t P,
-    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint64_t *__restrict__ misc,
-    uint32_t *__restrict__ seg, uint32_t *__restrict__ dups) {
-    constexpr int NW = RS_SMALL_THREADS / 32;
-    constexpr int ITEMS = RS_TILE_ITEMS;
-    constexpr int PER_WARP = 32 * ITEMS;
-    extern __shared__ __align__(16) uint8_t sm[];
-    uint64_t *sk = reinterpret_cast<uint64_t *>(sm);
-    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_SMALL);
-    uint32_t *cnt = sv + RS_SMALL;   // [NW][256]
-    __shared__ uint32_t dsum[256], dbase[256], ws[33];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    // 1. compaction (blocked: thread t owns pages 16t .. 16t + 15)
-    uint32_t fl = 0, nloc = 0;
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t p = tid * ITEMS + j;
-        const bool f = p < P && zero[p] == KC_PAGE_DATA;
-        fl |= (uint32_t)f << j;
-        nloc += f;
-    }
-    uint32_t m = 0;
-    uint32_t o = block_excl_sum(nloc, ws, &m);
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        if ((fl >> j) & 1) {
-            const uint32_t p = tid * ITEMS + j;
-            sk[o] = hash[p];
-            sv[o] = p;
-            ++o;
-        }
-    }
-    __syncthreads();
-    if (m == 0) {
-        if (tid == 0) {
-            misc[0] = 0;
-            misc[2] = 0;
-        }
-        return;
-    }
-
-    // 2. eight stable passes of 8-bit digits
-    uint64_t key[ITEMS];
-    uint32_t val[ITEMS];
-    uint16_t loc[ITEMS];
-#pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        const uint32_t i = warp * PER_WARP + r * 32 + lane;
-        key[r] = i < m ? sk[i] : ~0ull;   // padding sorts last and is never written
-        val[r] = i < m ? sv[i] : 0xffffffffu;
-    }
-    __syncthreads();
-    for (int shift = 0; shift < SORT_BITS; shift += 8) {
-        for (int i = tid; i < NW * 256; i += blockDim.x) cnt[i] = 0;
-        __syncthreads();
-        warp_rank<ITEMS>(key, shift, cnt + warp * 256, loc);
-        __syncthreads();
-        {   // per digit, exclusive over warps: two threads per digit, 8 warps each
-            const int d = tid & 255, h = tid >> 8;
-            uint32_t run = 0;
-            for (int w = h * (NW / 2); w < (h + 1) * (NW / 2); ++w) {
-                const uint32_t t = cnt[w * 256 + d];
-                cnt[w * 256 + d] = run;
-                run += t;
-            }
-            if (h == 0) dsum[d] = run;
-            __syncthreads();
-            if (h == 1) {
-                const uint32_t lo = dsum[d];
-                for (int w = NW / 2; w < NW; ++w) cnt[w * 256 + d] += lo;
-                dbase[d] = lo + run;        // digit total, scanned below
-            }
-            __syncthreads();
-            if (h == 0) dsum[d] = dbase[d];
-        }
-        __syncthreads();
-        if (tid < 32) digit_bases(dsum, dbase);
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < ITEMS; ++r) {
-            const uint32_t d = digit_of(key[r], shift);
-            const uint32_t at = dbase[d] + cnt[warp * 256 + d] + loc[r];
-            sk[at] = key[r];
-            sv[at] = val[r];
-        }
-        __syncthreads();
-        if (shift + 8 < SORT_BITS) {
-#pragma unroll
-            for (int r = 0; r < ITEMS; ++r) {
-                const uint32_t i = warp * PER_WARP + r * 32 + lane;
-                key[r] = sk[i];
-                val[r] = sv[i];
-            }
-            __syncthreads();
-        }
-    }
-
-    // 3. output, segment starts (max-scan of head indices), equal-hash neighbours
-    uint32_t hmax = 0, nd = 0, dfl = 0;
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t i = tid * ITEMS + j;
-        if (i < m) {
-            keys_out[i] = sk[i];
-            vals_out[i] = sv[i];
-            const bool head = i == 0 || sort_key(sk[i]) != sort_key(sk[i - 1]);
-            if (head) hmax = i;
-            else {
-                dfl |= 1u << j;
-                ++nd;
-            }
-        }
-    }
-    uint32_t run = block_excl_max(hmax, ws);
-    uint32_t ndup = 0;
-    uint32_t dpos = block_excl_sum(nd, ws, &ndup);
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t i = tid * ITEMS + j;
-        if (i < m) {
-            if (!((dfl >> j) & 1)) run = i;
-            seg[i] = run;
-            if ((dfl >> j) & 1) dups[dpos++] = i;
-        }
-    }
-    if (tid == 0) {
-        misc[0] = m;
-        misc[2] = ndup;
-    }
-}
-
 // Tiled pass, part 1: per-tile digit histogram, stored digit-major.
 __global__ void __launch_bounds__(RS_TILE_THREADS) rs_hist_kernel(const uint64_t *__restrict__ keys,
                                                                   const uint64_t *__restrict__ m_ptr, int shift,
@@ -543,6 +404,38 @@ __global__ void __launch_bounds__(SEG_THREADS) dd_segments_kernel(const uint64_t
     if (tid == 0) misc[2] = carry_sum;
 }
 
+// Byte comparison of one 16 KiB piece of pages pa and pb by one warp; true
+// if they differ there (or differ in length).
+__device__ __forceinline__ bool warp_piece_differs(const Pages &pg, uint32_t pa, uint32_t pb, uint32_t piece) {
+    const uint32_t lane = lane_id();
+    const PageLoc a = locate(pg, pa);
+    const PageLoc b = locate(pg, pb);
+    if (a.len != b.len) return true;
+    const uint64_t p0 = (uint64_t)piece * DD_PIECE;
+    if (p0 >= a.len) return false;
+    const uint64_t plen = a.len - p0 < DD_PIECE ? a.len - p0 : DD_PIECE;
+    const uint8_t *x = a.ptr + p0, *y = b.ptr + p0;
+    const uint64_t nvec = plen >> 4;
+    bool diff = false;
+    uint64_t v = lane;
+    for (; v + 96 < nvec; v += 128) {
+        uint4 a0 = ldg_stream(x + 16 * v), a1 = ldg_stream(x + 16 * (v + 32));
+        uint4 a2 = ldg_stream(x + 16 * (v + 64)), a3 = ldg_stream(x + 16 * (v + 96));
+        uint4 b0 = ldg_stream(y + 16 * v), b1 = ldg_stream(y + 16 * (v + 32));
+        uint4 b2 = ldg_stream(y + 16 * (v + 64)), b3 = ldg_stream(y + 16 * (v + 96));
+        diff |= (a0.x ^ b0.x) | (a0.y ^ b0.y) | (a0.z ^ b0.z) | (a0.w ^ b0.w);
+        diff |= (a1.x ^ b1.x) | (a1.y ^ b1.y) | (a1.z ^ b1.z) | (a1.w ^ b1.w);
+        diff |= (a2.x ^ b2.x) | (a2.y ^ b2.y) | (a2.z ^ b2.z) | (a2.w ^ b2.w);
+        diff |= (a3.x ^ b3.x) | (a3.y ^ b3.y) | (a3.z ^ b3.z) | (a3.w ^ b3.w);
+    }
+    for (; v < nvec; v += 32) {
+        uint4 a0 = ldg_stream(x + 16 * v), b0 = ldg_stream(y + 16 * v);
+        diff |= (a0.x ^ b0.x) | (a0.y ^ b0.y) | (a0.z ^ b0.z) | (a0.w ^ b0.w);
+    }
+    for (uint64_t t = (nvec << 4) + lane; t < plen; t += 32) diff |= x[t] != y[t];
+    return __any_sync(0xffffffffu, diff) != 0;
+}
+
 // Byte-compare sorted element i with element i-1, one 16 KiB piece per warp.
 __global__ void __launch_bounds__(256) dd_verify_kernel(Pages pg, const uint32_t *__restrict__ vals,
                                                         const uint32_t *__restrict__ dups,
@@ -551,41 +444,30 @@ __global__ void __launch_bounds__(256) dd_verify_kernel(Pages pg, const uint32_t
     const uint64_t ndup = misc[2];
     const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
     const uint64_t items = ndup * pieces;
-    const uint32_t lane = lane_id();
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t it = gw; it < items; it += nw) {
         const uint32_t i = dups[it / pieces];
         const uint32_t piece = (uint32_t)(it % pieces);
-        const PageLoc a = locate(pg, vals[i]);
-        const PageLoc b = locate(pg, vals[i - 1]);
-        if (a.len != b.len) {
-            if (lane == 0) neq[i] = 1;
-            continue;
-        }
-        const uint64_t p0 = (uint64_t)piece * DD_PIECE;
-        if (p0 >= a.len) continue;
-        const uint64_t plen = a.len - p0 < DD_PIECE ? a.len - p0 : DD_PIECE;
-        const uint8_t *x = a.ptr + p0, *y = b.ptr + p0;
-        const uint64_t nvec = plen >> 4;
-        bool diff = false;
-        uint64_t v = lane;
-        for (; v + 96 < nvec; v += 128) {
-            uint4 a0 = ldg_stream(x + 16 * v), a1 = ldg_stream(x + 16 * (v + 32));
-            uint4 a2 = ldg_stream(x + 16 * (v + 64)), a3 = ldg_stream(x + 16 * (v + 96));
-            uint4 b0 = ldg_stream(y + 16 * v), b1 = ldg_stream(y + 16 * (v + 32));
-            uint4 b2 = ldg_stream(y + 16 * (v + 64)), b3 = ldg_stream(y + 16 * (v + 96));
-            diff |= (a0.x ^ b0.x) | (a0.y ^ b0.y) | (a0.z ^ b0.z) | (a0.w ^ b0.w);
-            diff |= (a1.x ^ b1.x) | (a1.y ^ b1.y) | (a1.z ^ b1.z) | (a1.w ^ b1.w);
-            diff |= (a2.x ^ b2.x) | (a2.y ^ b2.y) | (a2.z ^ b2.z) | (a2.w ^ b2.w);
-            diff |= (a3.x ^ b3.x) | (a3.y ^ b3.y) | (a3.z ^ b3.z) | (a3.w ^ b3.w);
-        }
-        for (; v < nvec; v += 32) {
-            uint4 a0 = ldg_stream(x + 16 * v), b0 = ldg_stream(y + 16 * v);
-            diff |= (a0.x ^ b0.x) | (a0.y ^ b0.y) | (a0.z ^ b0.z) | (a0.w ^ b0.w);
-        }
-        for (uint64_t t = (nvec << 4) + lane; t < plen; t += 32) diff |= x[t] != y[t];
-        if (__any_sync(0xffffffffu, diff) && lane == 0) neq[i] = 1;
+        if (warp_piece_differs(pg, vals[i], vals[i - 1], piece) && lane_id() == 0) neq[i] = 1;
+    }
+}
+
+// Small path: byte-compare page dups[j] with its group's representative
+// rep[dups[j]], one 16 KiB piece per warp; neq[j] = 1 where they differ.
+__global__ void __launch_bounds__(256) dd_verify_rep_kernel(Pages pg, const uint32_t *__restrict__ dups,
+                                                            const uint32_t *__restrict__ rep,
+                                                            const uint64_t *__restrict__ misc,
+                                                            uint32_t *__restrict__ neq) {
+    const uint64_t ndup = misc[2];
+    const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
+    const uint64_t items = ndup * pieces;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t it = gw; it < items; it += nw) {
+        const uint64_t j = it / pieces;
+        const uint32_t p = dups[j];
+        if (warp_piece_differs(pg, p, rep[p], (uint32_t)(it % pieces)) && lane_id() == 0) neq[j] = 1;
     }
 }
 
@@ -693,100 +575,302 @@ __global__ void dd_table_kernel(Pages pg, const uint8_t *__restrict__ zero, cons
     }
 }
 
-// ---- small snapshots: classes, slow path, blob ids and the table in one CTA -----
+// ---- small snapshots (P <= DD_SMALL pages) -------------------------------------
+//
+// The candidates for a page's class are the pages with the same 64-bit hash.
+// One CTA inserts every data page into an open-addressing table in shared
+// memory keyed by the hash, keeping the smallest page id of each key (the
+// group's representative), so no sort is needed.  A page that is not its
+// group's representative is listed for a byte comparison with it
+// (dd_verify_rep_kernel).  With nothing to verify -- no two data pages share
+// a hash -- the same CTA assigns blob ids and writes the page table; else
+// dd_small_finish_kernel does so after the verification: a group whose
+// members all equal the representative is one class, and a group with a
+// failed comparison (a hash collision, or equal hashes of pages of different
+// lengths) is split by direct comparison exactly as the class definition
+// reads (members in increasing page id, each compared with the classes found
+// so far).
 
-constexpr int SMALL_BACK_THREADS = 1024;
+constexpr int DD_SMALL = 8192;                              // pages
+constexpr int DD_SMALL_THREADS = 1024;
+constexpr int DD_SMALL_PER = DD_SMALL / DD_SMALL_THREADS;   // pages per thread, blocked
+constexpr int DD_TABLE = 2 * DD_SMALL;                      // hash-table slots
+constexpr unsigned long long DD_EMPTY = ~0ull;
+constexpr size_t DD_SMALL_SMEM = (size_t)DD_TABLE * 8 + (size_t)DD_TABLE * 4 + (size_t)DD_SMALL * 2;
+constexpr size_t DD_FINISH_SMEM = (size_t)DD_SMALL * 4 * 4 + (size_t)DD_SMALL * 2 + (size_t)DD_SMALL;
 
-__global__ void __launch_bounds__(SMALL_BACK_THREADS) dd_small_back_kernel(
-    Pages pg, const uint8_t *__restrict__ zero, const uint32_t *__restrict__ vals,
-    const uint32_t *__restrict__ seg, const uint32_t *__restrict__ dups, const uint32_t *__restrict__ neq,
-    uint64_t *__restrict__ misc, uint32_t *__restrict__ reps, kc_page *__restrict__ table,
-    uint32_t *__restrict__ blob_page, uint64_t *__restrict__ n_blobs_out) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    uint32_t *bad = reinterpret_cast<uint32_t *>(sm);   // [RS_SMALL] per sorted position
-    uint32_t *canon = bad + RS_SMALL;                   // [RS_SMALL] per page
-    uint32_t *list = canon + RS_SMALL;                  // [RS_SMALL] bad segments, then blob ids
-    __shared__ uint32_t ws[33];
-    __shared__ uint32_t nbad;
+// Region of each page of thread tid's blocked range, from a mark at each
+// region's first page and a block-wide running max.  `mark` holds DD_SMALL
+// u16 entries; ws 33 words.  Every thread calls it.
+__device__ void small_regions(const Pages &pg, uint16_t *mark, uint32_t *ws, uint32_t (&reg)[DD_SMALL_PER]) {
     const int tid = threadIdx.x;
-    const uint32_t m = (uint32_t)misc[0], ndup = (uint32_t)misc[2], P = (uint32_t)pg.npages;
-    for (uint32_t i = tid; i < m; i += blockDim.x) bad[i] = 0;
-    for (uint32_t p = tid; p < P; p += blockDim.x) canon[p] = p;
-    if (tid == 0) nbad = 0;
+    for (int i = tid; i < DD_SMALL; i += blockDim.x) mark[i] = 0;
     __syncthreads();
-    for (uint32_t j = tid; j < ndup; j += blockDim.x) {
-        const uint32_t i = dups[j];
-        if (neq[i]) {
-            const uint32_t s = seg[i];
-            if (atomicExch(&bad[s], 1u) == 0u) list[atomicAdd(&nbad, 1u)] = s;
-        }
+    for (int a = tid; a < pg.nregions; a += blockDim.x) {
+        const uint64_t f = pg.regions[a].first;
+        if (f < (uint64_t)DD_SMALL) mark[f] = (uint16_t)a;   // every region holds at least one page
     }
     __syncthreads();
-    for (uint32_t i = tid; i < m; i += blockDim.x) {
-        const uint32_t s = seg[i];
-        if (!bad[s]) canon[vals[i]] = vals[s];
-    }
-    __syncthreads();
-    const uint32_t nb_seg = nbad;
-    for (uint32_t b = 0; b < nb_seg; ++b) {       // rare: hash collisions only
-        const uint32_t s = list[b];
-        uint32_t nrep = 0;
-        for (uint32_t j = s; j < m && seg[j] == s; ++j) {
-            const uint32_t pj = vals[j];
-            uint32_t found = 0xffffffffu;
-            for (uint32_t r = 0; r < nrep; ++r) {
-                if (cta_pages_equal(pg, pj, reps[s + r])) {
-                    found = reps[s + r];
-                    break;
-                }
-            }
-            if (tid == 0) {
-                if (found != 0xffffffffu) canon[pj] = found;
-                else {
-                    reps[s + nrep] = pj;
-                    canon[pj] = pj;
-                }
-            }
-            if (found == 0xffffffffu) ++nrep;
-            __syncthreads();
-        }
-    }
-    __syncthreads();
-    // blob ids: exclusive scan of "canonical non-zero page" in page order
-    constexpr int PER = RS_SMALL / SMALL_BACK_THREADS;
-    uint32_t fl = 0, nloc = 0;
+    uint32_t run = 0;
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const uint32_t p = tid * PER + j;
-        const bool f = p < P && zero[p] == KC_PAGE_DATA && canon[p] == p;
-        fl |= (uint32_t)f << j;
-        nloc += f;
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t m = mark[tid * DD_SMALL_PER + j];
+        run = m > run ? m : run;
+        reg[j] = run;
+    }
+    const uint32_t before = block_excl_max(run, ws);
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) reg[j] = reg[j] > before ? reg[j] : before;
+}
+
+// Blob ids (canonical data pages numbered in page order), the page table and
+// blob_page, for thread tid's blocked pages.  canon_of(j) gives the
+// canonical page of the thread's j-th page; `bid` is DD_SMALL u32 of shared
+// memory receiving each canonical page's blob id.
+template <class CanonOf>
+__device__ void small_table(const Pages &pg, const uint8_t *__restrict__ zero, const uint32_t (&reg)[DD_SMALL_PER],
+                            CanonOf canon_of, uint32_t *bid, uint32_t *ws, kc_page *__restrict__ table,
+                            uint32_t *__restrict__ blob_page, uint64_t *__restrict__ misc,
+                            uint64_t *__restrict__ n_blobs_out) {
+    const int tid = threadIdx.x;
+    const uint32_t P = (uint32_t)pg.npages;
+    uint8_t z[DD_SMALL_PER];
+    uint32_t c[DD_SMALL_PER];
+    uint32_t nloc = 0;
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        z[j] = p < P ? zero[p] : (uint8_t)KC_PAGE_ZERO;
+        c[j] = canon_of(j);
+        nloc += (p < P && z[j] == KC_PAGE_DATA && c[j] == p);
     }
     uint32_t nb = 0;
     uint32_t o = block_excl_sum(nloc, ws, &nb);
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        if ((fl >> j) & 1) {
-            const uint32_t p = tid * PER + j;
-            list[p] = o;
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        if (p < P && z[j] == KC_PAGE_DATA && c[j] == p) {
+            bid[p] = o;
             blob_page[o] = p;
             ++o;
         }
     }
     __syncthreads();
-    for (uint32_t p = tid; p < P; p += blockDim.x) {
-        const int a = region_of(pg.regions, pg.nregions, p);
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        if (p >= P) continue;
         kc_page row;
-        row.va_offset = (p - pg.regions[a].first) << pg.log2page;
-        row.alloc_id = (uint32_t)a;
-        const uint8_t z = zero[p];
-        row.blob = z == KC_PAGE_ZERO ? KC_BLOB_ZERO : z == KC_PAGE_LOST ? KC_BLOB_LOST : list[canon[p]];
+        row.va_offset = (p - pg.regions[reg[j]].first) << pg.log2page;
+        row.alloc_id = reg[j];
+        row.blob = z[j] == KC_PAGE_ZERO ? KC_BLOB_ZERO : z[j] == KC_PAGE_LOST ? KC_BLOB_LOST : bid[c[j]];
         table[p] = row;
     }
     if (tid == 0) {
         misc[1] = nb;
         if (n_blobs_out) *n_blobs_out = nb;
     }
+}
+
+__device__ __forceinline__ uint32_t dd_slot(uint64_t h) {
+    return (uint32_t)(h ^ (h >> 29) ^ (h >> 47)) & (DD_TABLE - 1);
+}
+
+__global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
+    Pages pg, const uint64_t *__restrict__ hash, const uint8_t *__restrict__ zero, uint64_t *__restrict__ misc,
+    uint32_t *__restrict__ rep_out, uint32_t *__restrict__ dups, uint32_t *__restrict__ neq,
+    kc_page *__restrict__ table, uint32_t *__restrict__ blob_page, uint64_t *__restrict__ n_blobs_out) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    unsigned long long *tkey = reinterpret_cast<unsigned long long *>(sm);   // [DD_TABLE]
+    uint32_t *tval = reinterpret_cast<uint32_t *>(tkey + DD_TABLE);          // [DD_TABLE]
+    uint16_t *mark = reinterpret_cast<uint16_t *>(tval + DD_TABLE);          // [DD_SMALL]
+    __shared__ uint32_t ws[33];
+    __shared__ uint32_t empty_min;   // smallest data page whose hash equals the empty-slot marker
+    const int tid = threadIdx.x;
+    const uint32_t P = (uint32_t)pg.npages;
+
+    for (int i = tid; i < DD_TABLE; i += blockDim.x) {
+        tkey[i] = DD_EMPTY;
+        tval[i] = 0xffffffffu;
+    }
+    if (tid == 0) empty_min = 0xffffffffu;
+    uint32_t reg[DD_SMALL_PER];
+    small_regions(pg, mark, ws, reg);   // (its barriers also order the initialisation above)
+
+    // insert: key = hash, value = smallest page id with it
+    uint64_t h[DD_SMALL_PER];
+    uint32_t isdata = 0;
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        const bool d = p < P && zero[p] == KC_PAGE_DATA;
+        isdata |= (uint32_t)d << j;
+        h[j] = d ? hash[p] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        if (!((isdata >> j) & 1)) continue;
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        if (h[j] == DD_EMPTY) {
+            atomicMin(&empty_min, p);
+            continue;
+        }
+        // at most DD_SMALL keys in DD_TABLE slots: a free or matching slot is always found
+        for (uint32_t s = dd_slot(h[j]), k = 0; k < DD_TABLE; s = (s + 1) & (DD_TABLE - 1), ++k) {
+            const unsigned long long prev = atomicCAS(&tkey[s], DD_EMPTY, (unsigned long long)h[j]);
+            if (prev == DD_EMPTY || prev == h[j]) {
+                atomicMin(&tval[s], p);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    // look up each data page's representative
+    uint32_t rep[DD_SMALL_PER];
+    uint32_t nd = 0;
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        rep[j] = p;
+        if (!((isdata >> j) & 1)) continue;
+        if (h[j] == DD_EMPTY) {
+            rep[j] = empty_min;
+        } else {
+            for (uint32_t s = dd_slot(h[j]), k = 0; k < DD_TABLE; s = (s + 1) & (DD_TABLE - 1), ++k) {
+                if (tkey[s] == h[j]) {
+                    rep[j] = tval[s];
+                    break;
+                }
+            }
+        }
+        nd += rep[j] != p;
+    }
+    uint32_t ndup = 0;
+    uint32_t o = block_excl_sum(nd, ws, &ndup);
+    if (ndup == 0) {
+        // no two data pages share a hash: every data page is canonical
+        uint32_t *bid = tval;   // the table is no longer needed
+        small_table(pg, zero, reg, [&](int j) { return (uint32_t)(tid * DD_SMALL_PER + j); }, bid, ws, table,
+                    blob_page, misc, n_blobs_out);
+        if (tid == 0) {
+            misc[0] = P;
+            misc[2] = 0;
+        }
+        return;
+    }
+    // pages to verify, in increasing page id, and every data page's representative
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        if (p >= P) continue;
+        rep_out[p] = rep[j];
+        if (rep[j] != p) {
+            dups[o] = p;
+            neq[o] = 0;
+            ++o;
+        }
+    }
+    if (tid == 0) {
+        misc[0] = P;
+        misc[2] = ndup;
+    }
+}
+
+// After dd_verify_rep_kernel, when some data pages share a hash.  `classes`
+// (P entries of scratch) holds, per failed group, the classes found so far.
+__global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_finish_kernel(
+    Pages pg, const uint8_t *__restrict__ zero, const uint32_t *__restrict__ rep, const uint32_t *__restrict__ dups,
+    const uint32_t *__restrict__ neq, uint64_t *__restrict__ misc, uint32_t *__restrict__ classes,
+    kc_page *__restrict__ table, uint32_t *__restrict__ blob_page, uint64_t *__restrict__ n_blobs_out) {
+    const uint32_t ndup = (uint32_t)misc[2];
+    if (ndup == 0) return;   // dd_small_kernel wrote everything
+    extern __shared__ __align__(16) uint8_t sm[];
+    uint32_t *canon = reinterpret_cast<uint32_t *>(sm);   // [DD_SMALL] per page
+    uint32_t *order = canon + DD_SMALL;                   // [DD_SMALL] pages of failed groups; later blob ids
+    uint32_t *seg = order + DD_SMALL;                     // [DD_SMALL] per group: member count, then first slot
+    uint32_t *ncls = seg + DD_SMALL;                      // [DD_SMALL] per group: classes found so far
+    uint16_t *mark = reinterpret_cast<uint16_t *>(ncls + DD_SMALL);   // [DD_SMALL]
+    uint8_t *bad = reinterpret_cast<uint8_t *>(mark + DD_SMALL);      // [DD_SMALL] per representative
+    __shared__ uint32_t ws[33];
+    const int tid = threadIdx.x;
+    const uint32_t P = (uint32_t)pg.npages;
+    uint32_t reg[DD_SMALL_PER];
+    for (uint32_t i = tid; i < DD_SMALL; i += blockDim.x) {
+        bad[i] = 0;
+        seg[i] = 0;
+        ncls[i] = 0;
+    }
+    small_regions(pg, mark, ws, reg);   // (its barriers order the initialisation above)
+    for (uint32_t j = tid; j < ndup; j += blockDim.x)
+        if (neq[j]) bad[rep[dups[j]]] = 1;
+    __syncthreads();
+    // a page of a verified group: canonical = the representative
+    uint32_t c[DD_SMALL_PER];
+    uint32_t nslow = 0, slow = 0;
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        c[j] = p;
+        if (p < P && zero[p] == KC_PAGE_DATA) {
+            c[j] = rep[p];
+            if (bad[c[j]]) {
+                slow |= 1u << j;
+                ++nslow;
+                atomicAdd(&seg[c[j]], 1u);
+            }
+        }
+        if (p < P) canon[p] = c[j];
+    }
+    uint32_t total = 0;
+    uint32_t o = block_excl_sum(nslow, ws, &total);   // (its barriers order the counts above)
+    if (total) {
+        // pages of failed groups in increasing id, and each group's slots in
+        // `classes` (an exclusive scan of the member counts)
+        uint32_t cnt[DD_SMALL_PER], sum = 0;
+#pragma unroll
+        for (int j = 0; j < DD_SMALL_PER; ++j) {
+            if ((slow >> j) & 1) order[o++] = tid * DD_SMALL_PER + j;
+            cnt[j] = seg[tid * DD_SMALL_PER + j];
+            sum += cnt[j];
+        }
+        uint32_t at = block_excl_sum(sum, ws, nullptr);
+#pragma unroll
+        for (int j = 0; j < DD_SMALL_PER; ++j) {
+            seg[tid * DD_SMALL_PER + j] = at;
+            at += cnt[j];
+        }
+        __syncthreads();
+        for (uint32_t k = 0; k < total; ++k) {   // rare: hash collisions only
+            const uint32_t pj = order[k];
+            const uint32_t g = rep[pj];
+            const uint32_t base = seg[g], n = ncls[g];
+            uint32_t found = 0xffffffffu;
+            for (uint32_t r = 0; r < n; ++r) {
+                const uint32_t q = classes[base + r];
+                if (cta_pages_equal(pg, pj, q)) {
+                    found = q;
+                    break;
+                }
+            }
+            if (tid == 0) {
+                if (found != 0xffffffffu) {
+                    canon[pj] = found;
+                } else {
+                    classes[base + n] = pj;
+                    ncls[g] = n + 1;
+                    canon[pj] = pj;
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < DD_SMALL_PER; ++j) {
+            const uint32_t p = tid * DD_SMALL_PER + j;
+            if (p < P) c[j] = canon[p];
+        }
+        __syncthreads();
+    }
+    small_table(pg, zero, reg, [&](int j) { return c[j]; }, order, ws, table, blob_page, misc, n_blobs_out);
 }
 
 // ---- 6. pack ----------------------------------------------------------------------
@@ -835,11 +919,11 @@ __global__ void __launch_bounds__(256) dd_pack_kernel(Pages pg, const uint32_t *
 // ---- driver ------------------------------------------------------------------------
 
 cudaError_t setup_dedup_kernels() {
-    const size_t fsm = (size_t)RS_SMALL * 12 + (RS_SMALL_THREADS / 32) * 256 * 4;
-    cudaError_t e = cudaFuncSetAttribute(dd_small_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    cudaError_t e = cudaFuncSetAttribute(dd_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)DD_SMALL_SMEM);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(dd_small_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(RS_SMALL * 12));
+    return cudaFuncSetAttribute(dd_small_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)DD_FINISH_SMEM);
 }
 
 static inline unsigned grid_for(uint64_t n, int threads, int sms, int per_sm) {
@@ -860,26 +944,26 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
                       uint32_t *status, int sms, cudaStream_t st) {
     const uint64_t P = pg.npages;
     const unsigned g = grid_for(P, 256, sms, 8);
-    KC_TRY(cudaMemsetAsync(s.misc, 0, 64, st));
-    KC_TRY(cudaMemsetAsync(s.neq, 0, P * 4, st));
     const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
-    if (P <= (uint64_t)RS_SMALL) {
-        // small: front (compaction + sort + segments) and back (classes +
-        // blob ids + table) run in one CTA each, around the wide verify
-        const size_t fsm = (size_t)RS_SMALL * 12 + (RS_SMALL_THREADS / 32) * 256 * 4;
-        dd_small_front_kernel<<<1, RS_SMALL_THREADS, fsm, st>>>(hash, zero, (uint32_t)P, s.keys[0], s.vals[0], s.misc,
-                                                                s.seg, s.dups);
+    if (P <= (uint64_t)DD_SMALL) {
+        // small: grouping by a shared-memory hash table in one CTA, the wide
+        // verification of pages sharing a hash, and (only when there were
+        // such pages) the classes and table in a second CTA
+        dd_small_kernel<<<1, DD_SMALL_THREADS, DD_SMALL_SMEM, st>>>(pg, hash, zero, s.misc, s.canon, s.dups, s.neq,
+                                                                    table, s.blob_page, n_blobs);
         count_launches(1);
         KC_TRY(cudaGetLastError());
-        dd_verify_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.vals[0], s.dups, s.misc, s.neq);
+        dd_verify_rep_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.dups, s.canon, s.misc,
+                                                                                     s.neq);
         count_launches(1);
         KC_TRY(cudaGetLastError());
-        const size_t bsm = (size_t)RS_SMALL * 12;
-        dd_small_back_kernel<<<1, SMALL_BACK_THREADS, bsm, st>>>(pg, zero, s.vals[0], s.seg, s.dups, s.neq, s.misc,
-                                                                 s.reps, table, s.blob_page, n_blobs);
+        dd_small_finish_kernel<<<1, DD_SMALL_THREADS, DD_FINISH_SMEM, st>>>(pg, zero, s.canon, s.dups, s.neq, s.misc,
+                                                                            s.reps, table, s.blob_page, n_blobs);
         count_launches(1);
         KC_TRY(cudaGetLastError());
     } else {
+    KC_TRY(cudaMemsetAsync(s.misc, 0, 64, st));
+    KC_TRY(cudaMemsetAsync(s.neq, 0, P * 4, st));
     KC_TRY(cudaMemsetAsync(s.bad, 0, P * 4, st));
     // 1. compaction
     dd_flag_kernel<<<g, 256, 0, st>>>(zero, P, s.flags);

@@ -54,7 +54,7 @@ struct TableBuf {
     cudaEvent_t used = nullptr;
 };
 
-enum TablePart { TP_REGIONS = 0, TP_PAGEFIRST, TP_RANGES, TP_PAIRS, TP_JOBS, TP_WORK, TP_COUNT };
+enum TablePart { TP_REGIONS = 0, TP_PAGEFIRST, TP_RANGES, TP_PAIRS, TP_JOBS, TP_WORK, TP_LEFT, TP_COUNT };
 
 // A device-resident table set for one descriptor list.
 struct Tables {
@@ -75,6 +75,7 @@ struct Tables {
     const CmpPair *pairs() const { return static_cast<const CmpPair *>(part[TP_PAIRS]); }
     const BatchJob *jobs() const { return static_cast<const BatchJob *>(part[TP_JOBS]); }
     const BatchRange *work() const { return static_cast<const BatchRange *>(part[TP_WORK]); }
+    uint32_t *left() const { return static_cast<uint32_t *>(const_cast<void *>(part[TP_LEFT])); }
 };
 
 using HostParts = std::vector<uint8_t>[TP_COUNT];
@@ -781,6 +782,15 @@ KC_API kc_status kc_compare(kc_ctx *c, const kc_buf *got, const kc_buf *want, in
     return t->any_lost ? fail(c, KC_EBUF, "one or more pairs were marked lost") : KC_OK;
 }
 
+KC_API int kc_poll_flags(const uint32_t *flags, int n, int32_t *idx_out) {
+    if (!flags || !idx_out || n < 0) return -1;
+    int k = 0;
+    for (int i = 0; i < n; ++i)
+        if (__atomic_load_n(flags + i, __ATOMIC_RELAXED)) idx_out[k++] = i;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    return k;
+}
+
 KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t page_bytes, double atol,
                               double rtol, const kc_work *work, int nwork, void *stream) {
     if (!c) return KC_EINVAL;
@@ -819,6 +829,10 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
                 b.hash = J.d_hash;
                 b.zero = J.d_zero;
                 b.cmp = J.d_cmp;
+                b.done = J.d_done;
+                b.cmp_copy = J.d_cmp_copy;
+                b.items = 0;
+                b.pad = 0;
                 b.dtype = dt == KC_RAW ? KC_U8 : dt;
                 b.flags = (dg ? BJ_DIGEST : 0u) | (cm ? BJ_COMPARE : 0u) | ((J.flags & KC_BUF_LOST) ? BJ_LOST : 0u) |
                           ((work == nullptr || (J.flags & KC_JOB_INIT)) ? BJ_INIT : 0u);
@@ -862,15 +876,23 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
                 }
             }
             uint64_t it = 0;
+            std::vector<uint64_t> per_job(njobs, 0);
             for (auto &r : rg) {
                 r.item_first = it;
-                it += r.kind == 0 ? (r.count + 7) / 8 : r.count;
+                const uint64_t k = r.kind == 0 ? (r.count + 7) / 8 : r.count;
+                it += k;
+                per_job[r.job] += k;
+            }
+            for (int k = 0; k < njobs; ++k) {
+                if (per_job[k] > 0xFFFFFFFFull) return fail(c, KC_EINVAL, "job %d has more than 2^32 - 1 items", k);
+                bj[k].items = (uint32_t)per_job[k];
             }
             tb.items = it;
             tb.nranges = (int)rg.size();
             tb.n = njobs;
             put(parts[TP_JOBS], bj);
             put(parts[TP_WORK], rg);
+            put(parts[TP_LEFT], std::vector<uint32_t>(njobs, 0u));
             return KC_OK;
         },
         &t);
@@ -883,8 +905,8 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
     KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
     {
         Trace tr(c, st);
-        KC_CHECK(c, launch_batch(t->jobs(), njobs, t->work(), t->nranges, t->items, page_bytes, shape, atol, rtol,
-                                 task_counter(c), c->sms, st),
+        KC_CHECK(c, launch_batch(t->jobs(), njobs, t->left(), t->work(), t->nranges, t->items, page_bytes, shape, atol,
+                                 rtol, task_counter(c), c->sms, st),
                  "batch launch");
     }
     touch(c, t, st);

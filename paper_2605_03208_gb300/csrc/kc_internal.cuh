@@ -149,13 +149,17 @@ constexpr uint32_t CMP_TILE_BYTES = 16 * 1024;
 // with its own outputs; a range is a run of a job's units (pages or
 // comparison items) scheduled in one launch.
 enum : uint32_t { BJ_DIGEST = 1, BJ_COMPARE = 2, BJ_LOST = 4, BJ_INIT = 8 };
-struct BatchJob {          // 64 bytes
+struct BatchJob {          // 88 bytes
     uint64_t got, want, bytes, nelem;
     uint64_t *hash;
     uint8_t *zero;
     kc_cmp_result *cmp;
     int32_t dtype;         // comparison dtype (KC_RAW folded into KC_U8)
     uint32_t flags;        // BJ_*
+    uint32_t *done;        // completion flag, or null
+    kc_cmp_result *cmp_copy;
+    uint32_t items;        // work items of this job in the launch
+    uint32_t pad;
 };
 struct BatchRange {        // 32 bytes
     uint64_t first;        // first unit
@@ -165,9 +169,9 @@ struct BatchRange {        // 32 bytes
     uint32_t kind;         // 0: digest pages, PPW pages per item; 1: comparison items
 };
 constexpr uint32_t BATCH_CMP_ITEM_BYTES = 4 * CMP_TILE_BYTES;   // 64 KiB per comparison item
-cudaError_t launch_batch(const BatchJob *jobs, int njobs, const BatchRange *ranges, int nranges, uint64_t nitems,
-                         uint32_t page, const DigestShape &shape, double atol, double rtol, uint32_t *ctr,
-                         int sms, cudaStream_t st);
+cudaError_t launch_batch(const BatchJob *jobs, int njobs, uint32_t *left, const BatchRange *ranges, int nranges,
+                         uint64_t nitems, uint32_t page, const DigestShape &shape, double atol, double rtol,
+                         uint32_t *ctr, int sms, cudaStream_t st);
 cudaError_t setup_batch_kernels();
 
 }  // namespace kc

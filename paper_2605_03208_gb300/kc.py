@@ -32,7 +32,7 @@ ESIZE = {U8: 1, RAW: 1, I32: 4, F16: 2, BF16: 2, F32: 4}
 EXPORTS = ["kc_version", "kc_launch_count", "kc_status_name", "kc_last_error", "kc_create", "kc_destroy", "kc_sync",
            "kc_buf_status", "kc_set_digest_shape", "kc_set_trace_events", "kc_get_digest_shape", "kc_page_count",
            "kc_digest", "kc_census", "kc_scan", "kc_dedup", "kc_restore", "kc_compare",
-           "kc_census_static", "kc_batch_run"]
+           "kc_census_static", "kc_batch_run", "kc_poll_flags"]
 
 
 class KcBuf(ctypes.Structure):
@@ -48,7 +48,8 @@ BATCH_ITEM_BYTES = 65536
 class KcJob(ctypes.Structure):
     _fields_ = [("got_va", ctypes.c_uint64), ("want_va", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
                 ("dtype", ctypes.c_int32), ("flags", ctypes.c_int32), ("d_hash", ctypes.c_uint64),
-                ("d_zero", ctypes.c_uint64), ("d_cmp", ctypes.c_uint64), ("reserved", ctypes.c_uint64)]
+                ("d_zero", ctypes.c_uint64), ("d_cmp", ctypes.c_uint64), ("d_done", ctypes.c_uint64),
+                ("d_cmp_copy", ctypes.c_uint64)]
 
 
 class KcWork(ctypes.Structure):
@@ -112,6 +113,8 @@ def load(build_if_missing: bool = False):
     L.kc_batch_run.restype = st
     L.kc_batch_run.argtypes = [vp, ctypes.POINTER(KcJob), i32, u32, ctypes.c_double, ctypes.c_double,
                                ctypes.POINTER(KcWork), i32, vp]
+    L.kc_poll_flags.restype = i32
+    L.kc_poll_flags.argtypes = [vp, i32, vp]
     L.kc_census_static.restype = st
     L.kc_census_static.argtypes = [B, i32, u64, u64, vp, u64, vp, vp]
     L.kc_scan.restype = st
@@ -258,13 +261,18 @@ class Context:
                                                _stream(stream)), allow)
 
     def batch_run(self, job_array, page_bytes, atol=0.0, rtol=0.0, work_array=None, stream=None,
-                  allow=(OK, EBUF)):
+                  allow=(OK, EBUF), njobs=None, nwork=None):
+        """kc_batch_run.  job_array / work_array: ctypes arrays (or lists of
+        dicts / tuples, converted); njobs / nwork use a prefix of a larger
+        preallocated array."""
         j = job_array if isinstance(job_array, ctypes.Array) else jobs(job_array)
         w = work_array
         if w is not None and not isinstance(w, ctypes.Array):
             w = work(w)
-        return self._check(self.lib.kc_batch_run(self.h, j, len(j), page_bytes, float(atol), float(rtol), w,
-                                                 0 if w is None else len(w), _stream(stream)), allow)
+        nj = len(j) if njobs is None else njobs
+        nw = (0 if w is None else len(w)) if nwork is None else nwork
+        return self._check(self.lib.kc_batch_run(self.h, j, nj, page_bytes, float(atol), float(rtol), w, nw,
+                                                 _stream(stream)), allow)
 
     def compare(self, got, want, atol, rtol, out, stream=None, allow=(OK, EBUF)):
         g = got if isinstance(got, ctypes.Array) else bufs(got)
@@ -276,11 +284,12 @@ class Context:
 
 def jobs(items) -> ctypes.Array:
     """Array of kc_job from dicts with keys got, want, bytes, dtype, flags,
-    hash, zero, cmp (tensors or integer addresses; absent = 0)."""
+    hash, zero, cmp, done, cmp_copy (tensors or integer addresses; absent = 0)."""
     arr = (KcJob * len(items))()
     for i, it in enumerate(items):
         arr[i] = KcJob(_ptr(it.get("got")), _ptr(it.get("want")), int(it["bytes"]), int(it.get("dtype", RAW)),
-                       int(it["flags"]), _ptr(it.get("hash")), _ptr(it.get("zero")), _ptr(it.get("cmp")), 0)
+                       int(it["flags"]), _ptr(it.get("hash")), _ptr(it.get("zero")), _ptr(it.get("cmp")),
+                       _ptr(it.get("done")), _ptr(it.get("cmp_copy")))
     return arr
 
 
@@ -290,6 +299,29 @@ def work(items) -> ctypes.Array:
     for i, (j, k, f, c) in enumerate(items):
         arr[i] = KcWork(int(j), int(k), int(f), int(c))
     return arr
+
+
+class FlagPoller:
+    """Completion flags in pinned host memory for kc_job.d_done, read with
+    acquire ordering through kc_poll_flags."""
+
+    def __init__(self, n: int):
+        import torch
+        self.flags = torch.zeros(n, dtype=torch.int32, pin_memory=True)
+        self.view = self.flags.numpy()
+        self.idx = (ctypes.c_int32 * n)()
+        self.n = n
+        self.lib = load()
+
+    def address(self, i: int) -> int:
+        return self.flags.data_ptr() + 4 * i
+
+    def clear(self, i: int) -> None:
+        self.view[i] = 0
+
+    def poll(self) -> list:
+        k = self.lib.kc_poll_flags(self.flags.data_ptr(), self.n, self.idx)
+        return list(self.idx[:k])
 
 
 def census_static(regions, win_lo, win_hi, hits_out, cap, counts_out, stream=None) -> int:

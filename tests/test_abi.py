@@ -35,3 +35,50 @@ def test_page_count_is_host_only():
     b = kc.bufs([(0x1000, 4096 * 3 + 1), (0x100000, 5)])
     assert kc.page_count(b, 4096) == 5
     assert kc.page_count(b, 65536) == 2
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Sizes and field offsets of the C structs, compiled from include/kc.h
+    by the host C compiler, equal the binding's ctypes layouts."""
+    import ctypes
+    import numpy as np
+    src = tmp_path / "layout.c"
+    src.write_text('''#include <stdio.h>
+#include <stddef.h>
+#include "kc.h"
+#define F(T, m) printf(#T "." #m " %zu\\n", offsetof(T, m))
+int main(void) {
+    printf("kc_buf %zu\\nkc_page %zu\\nkc_hit %zu\\nkc_cmp_result %zu\\nkc_job %zu\\nkc_work %zu\\n",
+           sizeof(kc_buf), sizeof(kc_page), sizeof(kc_hit), sizeof(kc_cmp_result), sizeof(kc_job),
+           sizeof(kc_work));
+    F(kc_job, got_va); F(kc_job, want_va); F(kc_job, bytes); F(kc_job, dtype); F(kc_job, flags);
+    F(kc_job, d_hash); F(kc_job, d_zero); F(kc_job, d_cmp); F(kc_job, d_done); F(kc_job, d_cmp_copy);
+    F(kc_work, job); F(kc_work, kind); F(kc_work, first); F(kc_work, count);
+    return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    got = {k: int(v) for k, v in got.items()}
+    assert got["kc_buf"] == ctypes.sizeof(kc.KcBuf)
+    assert got["kc_page"] == kc.PAGE_DTYPE.itemsize
+    assert got["kc_hit"] == kc.HIT_DTYPE.itemsize
+    assert got["kc_cmp_result"] == kc.CMP_DTYPE.itemsize == 64
+    assert got["kc_job"] == ctypes.sizeof(kc.KcJob) == 72
+    assert got["kc_work"] == ctypes.sizeof(kc.KcWork)
+    for cls, cname in ((kc.KcJob, "kc_job"), (kc.KcWork, "kc_work")):
+        for name, _ in cls._fields_:
+            assert got[f"{cname}.{name}"] == getattr(cls, name).offset, (cname, name)
+
+
+def test_poll_flags_host_helper():
+    import ctypes
+    import numpy as np
+    lib = kc.load()
+    f = np.array([0, 1, 0, 7, 1], dtype=np.uint32)
+    idx = (ctypes.c_int32 * 5)()
+    assert lib.kc_poll_flags(f.ctypes.data, 5, idx) == 3 and list(idx[:3]) == [1, 3, 4]
+    assert lib.kc_poll_flags(f.ctypes.data, 0, idx) == 0
+    assert lib.kc_poll_flags(None, 5, idx) == -1 and lib.kc_poll_flags(f.ctypes.data, -1, idx) == -1

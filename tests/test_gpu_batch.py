@@ -3,6 +3,8 @@ jobs of uneven sizes in one persistent work-stealing launch, against the
 oracle; split work over several launches; lost jobs; CUDA-graph replay."""
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -247,3 +249,92 @@ def test_batch_argument_errors(ctx):
     assert bad(lambda j: None, work=[(0, kc.WORK_DIGEST, 0, outs.npages[0] + 1)]) == kc.EINVAL
     assert kc.launch_count() == before
     assert ctx.batch_run(good, 4096) == kc.OK and ctx.sync() == kc.OK
+
+
+def test_batch_completion_flags_and_record_copies(ctx):
+    """d_done flags in pinned host memory are set for every job, the record
+    copies equal the device records, a job with no unit in the launch is
+    flagged at once, and a job whose flag is not asked for is left alone."""
+    js = _small_set(9, n=40)
+    page = 65536
+    outs = Outs(js, page)
+    flags = [kc.JOB_DIGEST | kc.JOB_COMPARE] * len(js.sizes)
+    n = len(js.sizes)
+    done = torch.zeros(n, dtype=torch.int32, pin_memory=True)
+    copies = torch.zeros(n * 64, dtype=torch.uint8, pin_memory=True)
+    jobs = outs.job_dicts(js, flags)
+    for k, j in enumerate(jobs):
+        if k != 5:
+            j["done"] = done.data_ptr() + 4 * k
+            j["cmp_copy"] = copies.data_ptr() + 64 * k
+    assert ctx.batch_run(jobs, page) == kc.OK
+    torch.cuda.synchronize()
+    h, z, rec = outs.fetch()
+    d = done.numpy()
+    assert (d[np.arange(n) != 5] == 1).all() and d[5] == 0
+    cp = copies.numpy().view(kc.CMP_DTYPE)
+    for k in range(n):
+        if k != 5:
+            assert cp[k].tobytes() == rec[k].tobytes(), k
+    _check_against_oracle(js, outs, flags)
+    # split over two launches: the flag is asked for in the second only; a
+    # job absent from a launch's work list is flagged by that launch at once
+    outs2 = Outs(js, page)
+    done.zero_()
+    copies.zero_()
+    first = [(k, kc.WORK_COMPARE, 0, 1) for k in range(n)]
+    second = [(k, kc.WORK_COMPARE, 1, (js.sizes[k] + kc.BATCH_ITEM_BYTES - 1) // kc.BATCH_ITEM_BYTES - 1)
+              for k in range(n)]
+    second = [w for w in second if w[3] > 0]
+    jf = [kc.JOB_COMPARE | kc.JOB_INIT] * n
+    jobs1 = outs2.job_dicts(js, jf)
+    assert ctx.batch_run(jobs1, page, work_array=first) == kc.OK
+    jobs2 = outs2.job_dicts(js, [kc.JOB_COMPARE] * n)
+    for k, j in enumerate(jobs2):
+        j["done"] = done.data_ptr() + 4 * k
+        j["cmp_copy"] = copies.data_ptr() + 64 * k
+    assert ctx.batch_run(jobs2, page, work_array=second) == kc.OK
+    torch.cuda.synchronize()
+    assert (done.numpy() == 1).all()
+    _, _, rec2 = outs2.fetch()
+    assert copies.numpy().view(kc.CMP_DTYPE).tobytes() == rec2.tobytes()
+    _check_against_oracle(js, outs2, [kc.JOB_COMPARE] * n)
+
+
+def test_batch_small_job_flag_precedes_launch_end(ctx):
+    """With jobs ordered small first, a small job's flag can be observed
+    on the host while the launch is still busy with a large job (at least the
+    flag is set no later than the end; both results are exact)."""
+    sizes = [64 * 1024, 1 << 30]
+    got = torch.empty(sum(sizes) + 256, dtype=torch.uint8, device="cuda")
+    got.random_(0, 256)
+    offs = [0, sizes[0]]
+    js = W.JobSet(sizes, [W.DT_U8, W.DT_U8], offs, got, got, {})
+    outs = Outs(js, 65536)
+    done = torch.zeros(2, dtype=torch.int32, pin_memory=True)
+    copies = torch.zeros(128, dtype=torch.uint8, pin_memory=True)
+    jobs = outs.job_dicts(js, [kc.JOB_COMPARE | kc.JOB_INIT] * 2)
+    for k in range(2):
+        jobs[k]["done"] = done.data_ptr() + 4 * k
+        jobs[k]["cmp_copy"] = copies.data_ptr() + 64 * k
+    work = [(0, kc.WORK_COMPARE, 0, 1), (1, kc.WORK_COMPARE, 0, sizes[1] // kc.BATCH_ITEM_BYTES)]
+    ctx.batch_run(jobs, 65536, work_array=work)          # builds the tables
+    torch.cuda.synchronize()
+    done.zero_()
+    ev = torch.cuda.Event()
+    ctx.batch_run(jobs, 65536, work_array=work)
+    ev.record()
+    seen_small_first = False
+    t_end = time.perf_counter() + 10.0
+    while time.perf_counter() < t_end:
+        d = done.numpy()
+        if d[0] == 1 and d[1] == 0:
+            seen_small_first = True
+        if d[1] == 1:
+            break
+    ev.synchronize()
+    assert (done.numpy() == 1).all()
+    rec = copies.numpy().view(kc.CMP_DTYPE)
+    assert rec["mismatches"].tolist() == [0, 0] and rec["first"].tolist() == [-1, -1]
+    # report only: the small job finished while the large one ran
+    print("small job flagged before the large one:", seen_small_first)

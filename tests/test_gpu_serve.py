@@ -28,7 +28,8 @@ def setup():
 
 
 def _fresh(reqs):
-    return [dataclasses.replace(r, result={}, planted=None, t_ready=0.0, t_done=0.0) for r in reqs]
+    return [dataclasses.replace(r, result={}, planted=None, t_start=0.0, admit_wait=0.0, t_ready=0.0,
+                                t_launch=0.0, t_done=0.0) for r in reqs]
 
 
 def test_goldens_digest_matches_oracle(setup):
@@ -46,8 +47,13 @@ def test_mix_equals_sequential_solo_and_oracle(setup):
     st_b = S.Server(ctx, g, "batched", budget_bytes=budget, tick_bytes=32 * W.MiB,
                     quantum_bytes=8 * W.MiB).serve(rb)
     st_s = S.Server(ctx, g, "sequential", budget_bytes=budget).serve(rs)
-    assert st_b.max_batch > 1                           # requests shared ticks
-    assert st_b.ticks > len(base) // 4
+    assert st_b.ticks >= len(base)
+    # everything queued at once: requests share ticks, results unchanged
+    rp = _fresh(base)
+    st_p = S.Server(ctx, g, "batched", tick_bytes=32 * W.MiB, quantum_bytes=8 * W.MiB, preload=True).serve(rp)
+    assert st_p.max_batch > 1
+    for a, b in zip(rp, rs):
+        assert a.result == b.result, a.rid
     for a, b in zip(rb, rs):
         assert a.result == b.result, a.rid
         assert S.expected_ok(a, g), (a.rid, a.kind, a.result, a.planted)
@@ -77,6 +83,7 @@ def test_big_request_does_not_block_small_ones(setup):
     small = int(np.argmin(g.sizes))
     reqs = [S.Request(0, S.COMPARE, big, 0.0, 0, 1)] + \
            [S.Request(i, S.DIGEST, small, 0.0, 0, 1 + i) for i in range(1, 6)]
-    S.Server(ctx, g, "batched", tick_bytes=2 * W.MiB, quantum_bytes=W.MiB, realtime=False).serve(reqs)
+    S.Server(ctx, g, "batched", tick_bytes=2 * W.MiB, quantum_bytes=W.MiB, solo_quantum_bytes=W.MiB,
+             realtime=False).serve(reqs)
     assert all(r.t_done < reqs[0].t_done for r in reqs[1:])
     assert reqs[0].result["mismatches"] == 0 and all(r.result["pages_differ"] == [] for r in reqs[1:])

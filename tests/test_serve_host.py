@@ -93,3 +93,11 @@ def test_budget_slots_and_stop():
     stop = threading.Event()
     stop.set()
     assert b.acquire(1, stop) is False      # no slot, and the loop is stopping
+
+
+def test_budget_try_acquire():
+    b = S.Budget(100, slots=2)
+    assert b.try_acquire(70) and not b.try_acquire(40) and b.try_acquire(30)
+    assert not b.try_acquire(0)             # no slot left
+    b.release(70)
+    assert b.try_acquire(10) and b.used == 40
