@@ -199,6 +199,20 @@ def autotune(ctx: kc.Context, js, op: str = "digest+compare", pages=None, cache_
     ctx.set_digest_shape()
     if best is None:
         raise RuntimeError("autotune: no shape could be launched")
+    # confirmation: the best few of the sweep re-timed with more repetitions
+    # (one sweep timing is a few launches and can be off by several percent)
+    top = sorted(sweep, key=lambda r: r["ms"])[:6]
+    plans = {}
+    for rec in top:
+        S = rec["page_bytes"]
+        if S not in plans:
+            plans[S] = make_plan(js, S, flags)
+        ctx.set_digest_shape(rec["warps"], rec["stages"], rec["chunk"], 1)
+        rec["ms_confirm"] = min(_time_ms(lambda: run_batched(ctx, plans[S], stream=stream), max(reps, 5), stream)
+                                for _ in range(2))
+    del plans
+    ctx.set_digest_shape()
+    best = dict(min(top, key=lambda r: r["ms_confirm"]))
     best = dict(best, gpu=_gpu_name(), op=op, size_class=size_class(js.sizes), swept=len(sweep),
                 tuned_at=time.strftime("%Y-%m-%dT%H:%M:%S"))
     cache[key] = best
