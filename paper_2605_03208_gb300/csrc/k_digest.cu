@@ -1,7 +1,8 @@
 // k_digest.cu -- the page digest kernel (XXH64 seed 0 + zero flag, optionally
 // with the census pre-filter flag per page; hashing in digest_task.cuh) and
-// the census kernels: classification of flagged pages, the standalone count
-// pass, the ordered write pass, and a single-CTA scan.
+// the census kernels: the tail of the fused scan (count, look-back, ordered
+// write in one launch), the standalone count pass, the ordered write pass,
+// and a single-CTA scan.
 #include <cuda_runtime.h>
 
 #include "digest_task.cuh"
@@ -10,8 +11,9 @@
 
 namespace kc {
 
-// page_hits value of a page whose words must still be classified
-constexpr uint32_t HITS_PENDING = 0xFFFFFFFFu;
+// The fused digest leaves page_hits[p] = 0 for a page that cannot hold a
+// census hit and region index + 1 for a page whose words must still be
+// classified.
 
 size_t digest_smem_bytes(const DigestShape &s) {
     const size_t ppw = 8 * (size_t)(s.lanes == 2 ? 2 : 1);
@@ -21,16 +23,28 @@ size_t digest_smem_bytes(const DigestShape &s) {
 // One warp per task of PPW consecutive pages (8 with one XXH64 lane per
 // thread, 16 with two), tasks taken from a global ticket counter so warps
 // that finish early steal the rest; see digest_task.cuh for the hashing.
+//
+// Small set-up work of the call rides along at the start (no extra
+// launches): zeroing the census tail's ticket and chunk words and the
+// caller's census counts, and copying the page offsets to the caller.
 template <bool CENSUS, int LPT, int CHUNK>
 __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, uint64_t *__restrict__ hash,
                                                      uint8_t *__restrict__ zero,
                                                      uint32_t *__restrict__ page_hits,
                                                      uint32_t *__restrict__ task_ctr,
-                                                     uint32_t *__restrict__ status, int stages, int chunk) {
+                                                     uint32_t *__restrict__ status, int stages, int chunk,
+                                                     DigestAux aux) {
     constexpr int TPP = 4 / LPT;
     constexpr int PPW = 32 / TPP;
     extern __shared__ __align__(128) uint8_t smem[];
     (void)status;   // no waits here can time out: cp.async groups always complete
+    {
+        const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t i = gt; i < aux.nzero; i += nt) aux.zero_words[i] = 0ull;
+        if (aux.counts && gt < 2) aux.counts[gt] = 0ull;
+        for (uint64_t i = gt; i < aux.npf; i += nt) aux.pf_dst[i] = aux.pf_src[i];
+    }
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     uint8_t *ring = smem + (size_t)warp * stages * PPW * ((size_t)chunk + 32);
@@ -45,8 +59,10 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
         const uint8_t *src = nullptr;
         uint64_t len = 0;
         bool lost = false;
+        int ri = 0;
         if (valid) {
-            const Region r = pg.regions[region_of(pg.regions, pg.nregions, p)];
+            ri = region_of(pg.regions, pg.nregions, p);
+            const Region r = pg.regions[ri];
             const uint64_t off = (p - r.first) << pg.log2page;
             len = r.bytes - off < pg.page ? r.bytes - off : pg.page;
             src = reinterpret_cast<const uint8_t *>(r.base + off);
@@ -61,7 +77,7 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
             } else {
                 hash[p] = d.hash;
                 zero[p] = d.zero ? KC_PAGE_ZERO : KC_PAGE_DATA;
-                if (CENSUS) page_hits[p] = d.cand ? HITS_PENDING : 0u;
+                if (CENSUS) page_hits[p] = d.cand ? (uint32_t)ri + 1u : 0u;   // region + 1: still to classify
             }
         }
     }
@@ -161,85 +177,276 @@ __device__ __forceinline__ UnitSpan unit_span(const Pages &u, uint64_t unit) {
     return s;
 }
 
-// Count the hits of every unit whose page_hits entry is HITS_PENDING.
-__global__ void __launch_bounds__(CENSUS_THREADS) census_flagged_kernel(Pages u, CensusArgs ca,
-                                                                         uint32_t *__restrict__ unit_hits,
-                                                                         uint64_t *__restrict__ counts) {
-    __shared__ Range srg[SMEM_RANGES];
-    __shared__ uint32_t red_in[CENSUS_WARPS], red_out[CENSUS_WARPS];
-    const Range *rg = stage_ranges(ca, srg);
-    const int warp = threadIdx.x >> 5;
-    for (uint64_t unit = blockIdx.x; unit < u.npages; unit += gridDim.x) {
-        if (unit_hits[unit] != HITS_PENDING) continue;   // uniform across the CTA
-        const UnitSpan sp = unit_span(u, unit);
-        const uint64_t per = (sp.nwords + CENSUS_WARPS - 1) / CENSUS_WARPS;
-        const uint64_t wb = per * warp, we = wb + per < sp.nwords ? wb + per : sp.nwords;
-        uint32_t nin = 0, nout = 0;
-        if (wb < we) warp_census_range(ca, rg, sp.base, wb, we, sp.off, (uint32_t)sp.region, nullptr, 0, 0, nin, nout);
-        if (lane_id() == 0) {
-            red_in[warp] = nin;
-            red_out[warp] = nout;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t si = 0, so = 0;
-            for (int w = 0; w < CENSUS_WARPS; ++w) {
-                si += red_in[w];
-                so += red_out[w];
-            }
-            unit_hits[unit] = si + so;
-            if (si) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), (unsigned long long)si);
-            if (so) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), (unsigned long long)so);
-        }
-        __syncthreads();
-    }
-}
-
-cudaError_t launch_census_flagged(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits, uint64_t *counts,
-                                  int sms, cudaStream_t st) {
-    uint64_t blocks = units.npages;
-    const uint64_t maxb = (uint64_t)sms * 8;
-    if (blocks > maxb) blocks = maxb;
-    if (blocks == 0) return cudaSuccess;
-    census_flagged_kernel<<<(unsigned)blocks, CENSUS_THREADS, 0, st>>>(units, ca, unit_hits, counts);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 template <bool CENSUS, int LPT>
 static void launch_lanes(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const Pages &pg, const CensusArgs &ca,
                          uint64_t *hash, uint8_t *zero, uint32_t *page_hits, uint32_t *task_ctr, uint32_t *status,
-                         const DigestShape &shape) {
+                         const DigestShape &shape, const DigestAux &aux) {
     switch (shape.chunk) {
     case 512:
         digest_kernel<CENSUS, LPT, 512><<<grid, block, smem, st>>>(pg, ca, hash, zero, page_hits, task_ctr, status,
-                                                                   shape.stages, shape.chunk);
+                                                                   shape.stages, shape.chunk, aux);
         break;
     case 1024:
         digest_kernel<CENSUS, LPT, 1024><<<grid, block, smem, st>>>(pg, ca, hash, zero, page_hits, task_ctr, status,
-                                                                    shape.stages, shape.chunk);
+                                                                    shape.stages, shape.chunk, aux);
         break;
     default:
         digest_kernel<CENSUS, LPT, 0><<<grid, block, smem, st>>>(pg, ca, hash, zero, page_hits, task_ctr, status,
-                                                                 shape.stages, shape.chunk);
+                                                                 shape.stages, shape.chunk, aux);
     }
 }
 
 cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash, uint8_t *zero,
-                          uint32_t *page_hits, uint64_t *counts, uint32_t *task_ctr, uint32_t *status,
-                          const DigestShape &shape, cudaStream_t st) {
-    (void)counts;
+                          uint32_t *page_hits, uint32_t *task_ctr, uint32_t *status, const DigestShape &shape,
+                          const DigestAux &aux, cudaStream_t st) {
     const size_t smem = digest_smem_bytes(shape);
     const dim3 block(32 * shape.warps), grid(shape.ctas);
     CensusArgs none{};
     if (census && shape.lanes == 2)
-        launch_lanes<true, 2>(grid, block, smem, st, pg, *census, hash, zero, page_hits, task_ctr, status, shape);
+        launch_lanes<true, 2>(grid, block, smem, st, pg, *census, hash, zero, page_hits, task_ctr, status, shape, aux);
     else if (census)
-        launch_lanes<true, 1>(grid, block, smem, st, pg, *census, hash, zero, page_hits, task_ctr, status, shape);
+        launch_lanes<true, 1>(grid, block, smem, st, pg, *census, hash, zero, page_hits, task_ctr, status, shape, aux);
     else if (shape.lanes == 2)
-        launch_lanes<false, 2>(grid, block, smem, st, pg, none, hash, zero, nullptr, task_ctr, status, shape);
+        launch_lanes<false, 2>(grid, block, smem, st, pg, none, hash, zero, nullptr, task_ctr, status, shape, aux);
     else
-        launch_lanes<false, 1>(grid, block, smem, st, pg, none, hash, zero, nullptr, task_ctr, status, shape);
+        launch_lanes<false, 1>(grid, block, smem, st, pg, none, hash, zero, nullptr, task_ctr, status, shape, aux);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---- census tail of the fused scan: one kernel, decoupled look-back ---------------
+//
+// After the digest kernel, page_hits[p] is the region index + 1 for pages
+// holding a word that passed the pre-filter and 0 otherwise.  CTAs take
+// chunks of TAIL_CHUNK pages in ticket order.  For each chunk: (A) the
+// words of its flagged pages, taken as one sequence in page order, are split
+// evenly between the CTA's warps; each warp classifies its run, counts its
+// hits and keeps the first TAIL_STASH of them, in word order, in shared
+// memory; (B) warp 0 scans the warps' counts, publishes the chunk's total,
+// walks back over earlier chunks' published words until one carries an
+// inclusive prefix (decoupled look-back) and publishes this chunk's
+// inclusive prefix; (C) each warp stores its hits at prefix + the hits of
+// earlier warps: from its stash, or, if it found more than TAIL_STASH, by
+// classifying its run again and writing as it goes (mostly from L2).  A
+// chunk waits only on chunks whose tickets were taken before its own, by
+// CTAs that are running and publish their totals without waiting, so the
+// walk always ends; each wait is also bounded and reports ST_TIMEOUT if it
+// gives up.
+
+constexpr int TAIL_THREADS = 512;
+constexpr int TAIL_WARPS = TAIL_THREADS / 32;
+constexpr int TAIL_CHUNK = 32;     // most pages per chunk (one warp lane each when listing them)
+constexpr int TAIL_STASH = 32;     // hits a warp keeps in shared memory
+constexpr unsigned long long LB_AGG = 1ull << 62;      // chunk word: total of the chunk
+constexpr unsigned long long LB_PREFIX = 2ull << 62;   // chunk word: inclusive prefix
+constexpr unsigned long long LB_VALUE = (1ull << 62) - 1;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 20;
+
+// Span of page p of region ri.
+__device__ __forceinline__ UnitSpan page_span(const Pages &u, uint64_t p, int ri) {
+    UnitSpan sp;
+    sp.region = ri;
+    const Region r = u.regions[ri];
+    sp.off = (p - r.first) << u.log2page;
+    const uint64_t len = r.bytes - sp.off < u.page ? r.bytes - sp.off : u.page;
+    sp.base = reinterpret_cast<const uint8_t *>(r.base + sp.off);
+    sp.nwords = len >> 3;
+    return sp;
+}
+
+// Exclusive prefix of chunk c: warp 0 reads the words of 32 earlier chunks
+// at a time (nearest first), waits (bounded) until each is published, and
+// stops at the nearest inclusive prefix, adding the totals before it.
+__device__ __forceinline__ unsigned long long lookback(volatile unsigned long long *word, uint64_t c,
+                                                       uint32_t *status) {
+    const uint32_t lane = lane_id();
+    unsigned long long prefix = 0;
+    int64_t base = (int64_t)c - 1;
+    while (base >= 0) {
+        const int64_t j = base - (int64_t)lane;
+        unsigned long long w = LB_PREFIX;   // before the first chunk: prefix 0
+        if (j >= 0) w = word[j];
+        uint32_t spins = 0;
+        while (__any_sync(0xffffffffu, (w & ~LB_VALUE) == 0) && spins < LB_SPIN_LIMIT) {
+            __nanosleep(32);
+            if ((w & ~LB_VALUE) == 0) w = word[j];
+            ++spins;
+        }
+        if (__any_sync(0xffffffffu, (w & ~LB_VALUE) == 0)) {
+            if (lane == 0) set_status(status, ST_TIMEOUT);
+            w = LB_PREFIX;   // give up: the prefix is wrong, the status says so
+        }
+        const uint32_t pm = __ballot_sync(0xffffffffu, (w & LB_PREFIX) != 0);
+        const uint32_t upto = pm ? (uint32_t)__ffs(pm) - 1 : 31u;
+        unsigned long long v = lane <= upto ? (w & LB_VALUE) : 0ull;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (pm) break;
+        base -= 32;
+    }
+    return prefix;
+}
+
+// One warp's run [a, b) of the chunk's flagged-page word sequence: classify
+// (hits to `out`, up to `cap` of them, in word order) and count.
+__device__ __forceinline__ void tail_run(const Pages &u, const CensusArgs &ca, const Range *rg, uint64_t p0,
+                                         const uint32_t *preg, const uint32_t *fpage, const uint64_t *fstart,
+                                         int nflag, uint64_t a, uint64_t b, kc_hit *out, uint64_t cap,
+                                         uint32_t &nin, uint32_t &nout) {
+    nin = 0;
+    nout = 0;
+    for (int i = 0; i < nflag && a < b; ++i) {
+        const uint64_t s0 = fstart[i], s1 = fstart[i + 1];
+        if (s1 <= a) continue;
+        if (s0 >= b) break;
+        const uint64_t wb = (a > s0 ? a : s0) - s0, we = (b < s1 ? b : s1) - s0;
+        const uint64_t p = p0 + fpage[i];
+        const UnitSpan sp = page_span(u, p, (int)preg[fpage[i]] - 1);
+        uint32_t ni = 0, no = 0;
+        const uint64_t done = nin + nout;
+        warp_census_range(ca, rg, sp.base, wb, we, sp.off, (uint32_t)sp.region, out, done, cap, ni, no);
+        nin += ni;
+        nout += no;
+    }
+}
+
+__global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, CensusArgs ca,
+                                                                    const uint32_t *__restrict__ page_hits,
+                                                                    unsigned long long *__restrict__ tail,
+                                                                    uint64_t nchunks, uint32_t cpages,
+                                                                    kc_hit *__restrict__ hits, uint64_t cap,
+                                                                    uint64_t *__restrict__ counts,
+                                                                    uint32_t *__restrict__ status) {
+    __shared__ Range srg[SMEM_RANGES];
+    __shared__ kc_hit stash[TAIL_WARPS][TAIL_STASH];
+    __shared__ uint32_t preg[TAIL_CHUNK], fpage[TAIL_CHUNK];
+    __shared__ uint64_t fstart[TAIL_CHUNK + 1];
+    __shared__ uint32_t wn[TAIL_WARPS], win_s[TAIL_WARPS], wout_s[TAIL_WARPS];
+    __shared__ int s_nflag;
+    __shared__ unsigned long long s_chunk, s_prefix;
+    const Range *rg = stage_ranges(ca, srg);
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    unsigned long long *ticket = tail;
+    volatile unsigned long long *word = tail + 1;
+    while (true) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const uint64_t c = s_chunk;
+        if (c >= nchunks) break;
+        const uint64_t p0 = c * cpages;
+        const uint64_t p1 = p0 + cpages < u.npages ? p0 + cpages : u.npages;
+        if (warp == 0) {   // the flagged pages and their word offsets in the chunk's sequence
+            const uint64_t p = p0 + lane;
+            const uint32_t r = p < p1 ? page_hits[p] : 0u;
+            preg[lane] = r;
+            const uint64_t nw = r ? page_span(u, p, (int)r - 1).nwords : 0;
+            const uint32_t fm = __ballot_sync(0xffffffffu, r != 0);
+            uint64_t inc = nw;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= (uint32_t)o) inc += y;
+            }
+            if (r) {
+                const int slot = __popc(fm & lanemask_lt());
+                fpage[slot] = lane;
+                fstart[slot] = inc - nw;
+            }
+            if (lane == 31) {
+                fstart[__popc(fm)] = inc;
+                s_nflag = __popc(fm);
+            }
+        }
+        __syncthreads();
+        const int nflag = s_nflag;
+        uint64_t total = 0;
+        if (nflag) {
+            // (A) count, keeping the first hits of each warp
+            const uint64_t T = fstart[nflag];
+            const uint64_t a = T * warp / TAIL_WARPS, b = T * (warp + 1) / TAIL_WARPS;
+            uint32_t nin, nout;
+            tail_run(u, ca, rg, p0, preg, fpage, fstart, nflag, a, b, stash[warp], TAIL_STASH, nin, nout);
+            if (lane == 0) {
+                wn[warp] = nin + nout;
+                win_s[warp] = nin;
+                wout_s[warp] = nout;
+            }
+            __syncthreads();
+            for (int w = 0; w < TAIL_WARPS; ++w) total += wn[w];
+        }
+        // (B) publish the total, look back, publish the inclusive prefix
+        if (warp == 0) {
+            unsigned long long prefix = 0;
+            if (c == 0) {
+                if (lane == 0) word[0] = LB_PREFIX | total;
+            } else {
+                if (lane == 0) word[c] = LB_AGG | total;
+                prefix = lookback(word, c, status);
+                if (lane == 0) word[c] = LB_PREFIX | (prefix + total);
+            }
+            if (lane == 0) {
+                s_prefix = prefix;
+                if (hits && prefix + total > cap) set_status(status, ST_TRUNC);
+                if (nflag) {
+                    uint32_t si = 0, so = 0;
+                    for (int w = 0; w < TAIL_WARPS; ++w) {
+                        si += win_s[w];
+                        so += wout_s[w];
+                    }
+                    if (si) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[0]), (unsigned long long)si);
+                    if (so) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[1]), (unsigned long long)so);
+                }
+            }
+        }
+        __syncthreads();
+        // (C) ordered write
+        if (hits && total) {
+            uint64_t before = s_prefix;
+            for (int w = 0; w < warp; ++w) before += wn[w];
+            const uint32_t n = wn[warp];
+            if (n <= (uint32_t)TAIL_STASH) {
+                for (uint32_t i = lane; i < n; i += 32)
+                    if (before + i < cap) hits[before + i] = stash[warp][i];
+            } else {
+                const uint64_t T = fstart[nflag];
+                const uint64_t a = T * warp / TAIL_WARPS, b = T * (warp + 1) / TAIL_WARPS;
+                uint32_t nin, nout;
+                tail_run(u, ca, rg, p0, preg, fpage, fstart, nflag, a, b, hits + before, cap > before ? cap - before : 0,
+                         nin, nout);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Pages per chunk: enough chunks for every resident CTA to take one, as
+// few as 8 pages and at most TAIL_CHUNK.
+static uint32_t tail_chunk_pages(uint64_t npages, int sms) {
+    const uint64_t ctas = (uint64_t)sms * 2;   // resident CTAs (2 per SM by registers)
+    uint64_t cp = (npages + ctas - 1) / ctas;
+    if (cp < 8) cp = 8;
+    if (cp > (uint64_t)TAIL_CHUNK) cp = TAIL_CHUNK;
+    return (uint32_t)cp;
+}
+
+uint64_t census_tail_chunks(uint64_t npages, int sms) {
+    const uint32_t cp = tail_chunk_pages(npages, sms);
+    return (npages + cp - 1) / cp;
+}
+
+cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
+                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, int sms,
+                               cudaStream_t st) {
+    const uint32_t cp = tail_chunk_pages(pg.npages, sms);
+    const uint64_t nchunks = (pg.npages + cp - 1) / cp;
+    if (nchunks == 0) return cudaSuccess;
+    uint64_t blocks = nchunks;
+    const uint64_t maxb = (uint64_t)sms * 2;
+    if (blocks > maxb) blocks = maxb;
+    census_tail_kernel<<<(unsigned)blocks, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, nchunks, cp,
+                                                                  cap ? hits : nullptr, cap, counts, status);
     count_launches(1);
     return cudaGetLastError();
 }

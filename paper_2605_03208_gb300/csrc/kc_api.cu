@@ -616,28 +616,34 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
     const Pages pg = make_pages(t->regions(), n, P, page_bytes);
     const DigestShape shape = pick_shape(c, page_bytes, P);
     uint32_t *page_hits = nullptr;
-    uint64_t *page_off = nullptr;
+    unsigned long long *tail = nullptr;
+    DigestAux aux;
     if (census) {
+        // page_hits[P] | census tail: ticket + one word per chunk of pages
+        const uint64_t nwords = 1 + census_tail_chunks(P, c->sms);
         void *scr = nullptr;
-        if ((s = scratch(c, P * 4 + 256 + P * 8, st, &scr)) != KC_OK) return s;
+        if ((s = scratch(c, ((P * 4 + 255) & ~255ull) + nwords * 8, st, &scr)) != KC_OK) return s;
         page_hits = static_cast<uint32_t *>(scr);
-        page_off = reinterpret_cast<uint64_t *>(static_cast<char *>(scr) + ((P * 4 + 255) & ~255ull));
-        KC_CHECK(c, cudaMemsetAsync(d_counts, 0, 16, st), "census counts clear");
+        tail = reinterpret_cast<unsigned long long *>(static_cast<char *>(scr) + ((P * 4 + 255) & ~255ull));
+        aux.zero_words = tail;
+        aux.nzero = nwords;
+        aux.counts = d_counts;
+    }
+    if (d_page_first) {
+        aux.pf_src = t->page_first();
+        aux.pf_dst = d_page_first;
+        aux.npf = (uint64_t)n + 1;
     }
     KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
     {
         Trace tr(c, st);
-        KC_CHECK(c, launch_digest(pg, census ? &t->ca : nullptr, d_hash, d_zero, page_hits, d_counts, task_counter(c),
-                                  status_word(c), shape, st),
+        KC_CHECK(c, launch_digest(pg, census ? &t->ca : nullptr, d_hash, d_zero, page_hits, task_counter(c),
+                                  status_word(c), shape, aux, st),
                  "digest launch");
     }
-    if (d_page_first)
-        KC_CHECK(c, cudaMemcpyAsync(d_page_first, t->page_first(), (n + 1) * 8, cudaMemcpyDeviceToDevice, st),
-                 "page_first copy");
-    if (census) {
-        KC_CHECK(c, launch_census_flagged(pg, t->ca, page_hits, d_counts, c->sms, st), "census classify");
-        if ((s = census_tail(c, pg, t->ca, page_hits, page_off, d_hits, cap, st)) != KC_OK) return s;
-    }
+    if (census)
+        KC_CHECK(c, launch_census_tail(pg, t->ca, page_hits, tail, d_hits, cap, d_counts, status_word(c), c->sms, st),
+                 "census tail");
     touch(c, t, st);
     return lost_status(c, t);
 }

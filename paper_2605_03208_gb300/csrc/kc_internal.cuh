@@ -79,19 +79,29 @@ cudaError_t setup_digest_kernels();
 cudaError_t setup_dedup_kernels();
 
 // Launchers (each returns the cudaError_t of its launch).
+// Set-up work done by the digest kernel's threads before hashing.
+struct DigestAux {
+    unsigned long long *zero_words = nullptr;   // zeroed (census tail ticket + chunk words)
+    uint64_t nzero = 0;
+    uint64_t *counts = nullptr;                 // caller's census counts, zeroed
+    const uint64_t *pf_src = nullptr;           // page offsets copied to the caller
+    uint64_t *pf_dst = nullptr;
+    uint64_t npf = 0;
+};
 // `census` NULL: digest only.  Otherwise page_hits[P] receives 0 for pages
 // that cannot hold a census hit and a pending mark for the others, which
-// launch_census_flagged then resolves.
-cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash,
-                          uint8_t *zero, uint32_t *page_hits, uint64_t *counts,
-                          uint32_t *task_ctr, uint32_t *status, const DigestShape &shape,
-                          cudaStream_t st);
+// launch_census_tail then resolves.
+cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash, uint8_t *zero,
+                          uint32_t *page_hits, uint32_t *task_ctr, uint32_t *status, const DigestShape &shape,
+                          const DigestAux &aux, cudaStream_t st);
+// Census of the fused scan after the digest kernel (one launch).  tail:
+// 1 + census_tail_chunks(P, sms) words zeroed by the digest kernel.
+uint64_t census_tail_chunks(uint64_t npages, int sms);
+cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
+                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, int sms,
+                               cudaStream_t st);
 cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
                                 uint64_t *counts, int sms, cudaStream_t st);
-// Classify the units the fused digest flagged (page_hits == pending):
-// exact per-unit hit counts, totals added to counts[2].
-cudaError_t launch_census_flagged(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
-                                  uint64_t *counts, int sms, cudaStream_t st);
 cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca,
                                 const uint32_t *unit_hits, const uint64_t *unit_off,
                                 kc_hit *hits, uint64_t cap, uint32_t *status, int sms,

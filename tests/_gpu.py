@@ -60,7 +60,7 @@ def run_scan(ctx, snap, dev, win, cap=None, page_bytes=None):
     z = torch.empty(max(P, 1), dtype=torch.uint8, device="cuda")
     pf = torch.empty(len(dev) + 1, dtype=torch.int64, device="cuda")
     hits = empty_u8(max(cap, 1) * 24)
-    counts = torch.zeros(2, dtype=torch.int64, device="cuda")
+    counts = torch.full((2,), 0x5A5A5A5A, dtype=torch.int64, device="cuda")   # the call resets them
     st = ctx.scan(b, S, h, z, pf, win[0], win[1], hits, cap, counts)
     return st, dict(hash=to_np(h)[:P].view(np.uint64), zero=to_np(z)[:P],
                     page_first=to_np(pf).view(np.uint64), hits=to_np(hits).view(kc.HIT_DTYPE),

@@ -97,6 +97,30 @@ def test_scan_fused_matches_digest_and_census(ctx, tiny):
     assert set(snap.truth["pointers"]) <= set(G.hits_tuples(r["hits"][:n]))
 
 
+@pytest.mark.parametrize("page", [4096, 65536])
+def test_scan_dense_pointers_many_chunks(ctx, page):
+    """The fused scan's census tail over many chunks of pages, most of them
+    holding hits (look-back across chunks), with truncation and count-only."""
+    layout = W.tiny_layout(3, n=12, total=6 * W.MiB)
+    snap, dev = G.device_snapshot(layout, W.tiny_fill, 3, p_ptr=0.6, p_zero=0.1)
+    win = W.default_window(snap.bases, snap.sizes)
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert nin + nout > 100000
+    st, r = G.run_scan(ctx, snap, dev, win, page_bytes=page)
+    assert ctx.sync() == kc.OK
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][: nin + nout]) == G.hits_tuples(ohits)
+    oh, oz, _ = _oracle_digest(snap, page)
+    assert np.array_equal(r["hash"], oh) and np.array_equal(r["zero"], oz)
+    cap = 777
+    st, r = G.run_scan(ctx, snap, dev, win, cap=cap, page_bytes=page)
+    assert ctx.sync() == kc.ETRUNC
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][:cap]) == G.hits_tuples(ohits[:cap])
+    st, r = G.run_scan(ctx, snap, dev, win, cap=0, page_bytes=page)
+    assert ctx.sync() == kc.OK and (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+
+
 def test_census_standalone(ctx, tiny):
     snap, dev = tiny
     win = W.default_window(snap.bases, snap.sizes)
