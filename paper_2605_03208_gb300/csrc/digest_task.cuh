@@ -15,15 +15,17 @@
 // pages' shared loads spread over all 32 banks.  The < 32-byte tail of a
 // page is read from global memory by the page leader while it finishes.
 //
-// The serial chain per accumulator is the critical path: each step is an
-// add, a rotate and a multiply by PRIME1 (xx_step); the lane products
+// The serial chain per accumulator is the critical path; it is carried in
+// pre-rotate form (xx_t_step: two funnel shifts, a 32 x 32 -> 64
+// multiply-add, two 32-bit multiplies and an add), and the lane products
 // (lane * PRIME2) and the next stripes' shared loads are issued ahead of it.
 // CHUNK (compile-time, 0 = none) gives full chunks of that size a fully
 // unrolled path.
 //
-// Census pre-filter: the hashing loop keeps, per page, the minimum of
-// (high 32 bits of a word - pre_lo), a branch-free conservative test of
-// whether any word can be a census hit.
+// Zero flag: one 32-bit OR of both halves of every word.  Census
+// pre-filter: the minimum over words of (high 32 bits - pre_lo), taken
+// pairwise, a branch-free conservative test of whether any word can be a
+// census hit.
 #pragma once
 
 #include "kc_device.cuh"
@@ -71,10 +73,10 @@ __device__ __forceinline__ PageDigest digest_pages(uint8_t *ring, int stages, in
     };
     for (int c = 0; c < stages - 1; ++c) issue((uint32_t)c);
 
-    uint64_t acc[LPT];
+    uint64_t acc[LPT];   // chain state t (pre-rotate form)
 #pragma unroll
-    for (int i = 0; i < LPT; ++i) acc[i] = xx_init(j * LPT + i);
-    uint32_t zlo = 0, zhi = 0;
+    for (int i = 0; i < LPT; ++i) acc[i] = xx_t_init(j * LPT + i);
+    uint32_t zor32 = 0;
     uint32_t cmin = 0xFFFFFFFFu;
     for (uint32_t c = 0; c < maxch; ++c) {
         issue(c + stages - 1);        // refills the stage consumed in the previous iteration
@@ -100,8 +102,7 @@ __device__ __forceinline__ PageDigest digest_pages(uint8_t *ring, int stages, in
         auto eat = [&](const uint64_t (&w)[LPT]) {
 #pragma unroll
             for (int i = 0; i < LPT; ++i) {
-                zlo |= (uint32_t)w[i];
-                zhi |= (uint32_t)(w[i] >> 32);
+                zor32 |= (uint32_t)w[i] | (uint32_t)(w[i] >> 32);
                 if (CENSUS) cmin = min(cmin, census_pre(ca, w[i]));
             }
         };
@@ -114,9 +115,15 @@ __device__ __forceinline__ PageDigest digest_pages(uint8_t *ring, int stages, in
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], m[u][i]);
+                for (int i = 0; i < LPT; ++i) acc[i] = xx_t_step(acc[i], m[u][i]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) eat(w[u]);
+            for (int i = 0; i < LPT; ++i) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) zor32 |= (uint32_t)w[u][i] | (uint32_t)(w[u][i] >> 32);
+                if (CENSUS)
+                    cmin = min(cmin, min(min(census_pre(ca, w[0][i]), census_pre(ca, w[1][i])),
+                                         min(census_pre(ca, w[2][i]), census_pre(ca, w[3][i]))));
+            }
         };
         uint32_t s = 0;
         if (CHUNK && b == (uint32_t)CHUNK) {
@@ -163,12 +170,14 @@ __device__ __forceinline__ PageDigest digest_pages(uint8_t *ring, int stages, in
             uint64_t w[LPT];
             ld(s, w);
 #pragma unroll
-            for (int i = 0; i < LPT; ++i) acc[i] = xx_step(acc[i], w[i] * XXP2);
+            for (int i = 0; i < LPT; ++i) acc[i] = xx_t_step(acc[i], w[i] * XXP2);
             eat(w);
         }
         __syncwarp();                 // the stage is free for the next refill
     }
     cp_async_wait(0);                 // trailing (empty) groups
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) acc[i] = xx_t_final(acc[i]);
 
     // Page reduction: accumulators to the page leader, OR of bytes, census flag.
     const int lead = lane - j;
@@ -183,7 +192,7 @@ __device__ __forceinline__ PageDigest digest_pages(uint8_t *ring, int stages, in
         a[2] = __shfl_sync(FULL, acc[0], lead + 1);
         a[3] = __shfl_sync(FULL, acc[LPT - 1], lead + 1);
     }
-    uint64_t zor = ((uint64_t)zhi << 32) | zlo;
+    uint64_t zor = zor32;
 #pragma unroll
     for (int o = 1; o < TPP; o <<= 1) {
         zor |= __shfl_xor_sync(FULL, zor, o);

@@ -223,4 +223,48 @@ __device__ __forceinline__ uint64_t xx_init(int k) {
     return k == 0 ? XXP1 + XXP2 : k == 1 ? XXP2 : k == 2 ? 0ULL : 0ULL - XXP1;
 }
 
+// ---- the lane chain in "pre-rotate" form ---------------------------------------
+//
+// One XXH64 round is acc' = rotl(acc + m, 31) * PRIME1 with m = lane *
+// PRIME2.  Carrying t = acc + m instead of acc gives t' = rotl(t, 31) *
+// PRIME1 + m', and the low product with m' added is a single 32 x 32 -> 64
+// multiply-add, so a round is two funnel shifts, three multiplies and an
+// add, four dependent steps (same value mod 2^64 as the round above).  The
+// chain starts from the t whose step yields the specification's initial
+// accumulator, t0 = rotr(acc0 * PRIME1^-1, 31) (PRIME1 is odd, so it is
+// invertible mod 2^64), and ends with acc = rotl(t, 31) * PRIME1.
+
+constexpr uint64_t inv_odd(uint64_t a) {   // a^-1 mod 2^64 by Newton's iteration, a odd
+    uint64_t x = a;                          // correct to 3 bits: a * a == 1 mod 8
+    for (int i = 0; i < 6; ++i) x *= 2 - a * x;
+    return x;
+}
+constexpr uint64_t XXP1_INV = inv_odd(XXP1);
+static_assert(XXP1 * XXP1_INV == 1, "PRIME1 inverse");
+constexpr uint64_t rotr_c(uint64_t x, int r) { return (x >> r) | (x << (64 - r)); }
+constexpr uint64_t xx_t0(uint64_t acc0) { return rotr_c(acc0 * XXP1_INV, 31); }
+
+__device__ __forceinline__ uint64_t xx_t_init(int k) {
+    return k == 0 ? xx_t0(XXP1 + XXP2) : k == 1 ? xx_t0(XXP2) : k == 2 ? xx_t0(0ULL) : xx_t0(0ULL - XXP1);
+}
+
+// t' = rotl(t, 31) * PRIME1 + m  (mod 2^64)
+__device__ __forceinline__ uint64_t xx_t_step(uint64_t t, uint64_t m) {
+    uint32_t olo, ohi;
+    asm("{\n\t.reg .u32 rl, rh, x;\n\t.reg .u64 w, mm;\n\t"
+        "shf.l.wrap.b32 rh, %2, %3, 31;\n\t"
+        "shf.l.wrap.b32 rl, %3, %2, 31;\n\t"
+        "mov.b64 mm, {%4, %5};\n\t"
+        "mad.wide.u32 w, rl, 0x85EBCA87, mm;\n\t"
+        "mul.lo.u32 x, rl, 0x9E3779B1;\n\t"
+        "mad.lo.u32 x, rh, 0x85EBCA87, x;\n\t"
+        "mov.b64 {%0, %1}, w;\n\t"
+        "add.u32 %1, %1, x;\n\t}"
+        : "=r"(olo), "=r"(ohi)
+        : "r"((uint32_t)t), "r"((uint32_t)(t >> 32)), "r"((uint32_t)m), "r"((uint32_t)(m >> 32)));
+    return ((uint64_t)ohi << 32) | olo;
+}
+
+__device__ __forceinline__ uint64_t xx_t_final(uint64_t t) { return rotl(t, 31) * XXP1; }
+
 }  // namespace kc
