@@ -577,10 +577,12 @@ __global__ void dd_table_kernel(Pages pg, const uint8_t *__restrict__ zero, cons
 
 // ---- small snapshots (P <= DD_SMALL pages) -------------------------------------
 //
-// The candidates for a page's class are the pages with the same 64-bit hash.
-// One CTA inserts every data page into an open-addressing table in shared
-// memory keyed by the hash, keeping the smallest page id of each key (the
-// group's representative), so no sort is needed.  A page that is not its
+// The candidates for a page's class are the pages whose hashes share their
+// low 32 bits (as in the sort of the large path).  One CTA inserts every
+// data page into an open-addressing table in shared memory keyed by those
+// bits (32-bit atomics), keeping the smallest page id of each key (the
+// group's representative), so no sort is needed.  Pages whose full hashes
+// differ fail the byte comparison like any collision.  A page that is not its
 // group's representative is listed for a byte comparison with it
 // (dd_verify_rep_kernel).  With nothing to verify -- no two data pages share
 // a hash -- the same CTA assigns blob ids and writes the page table; else
@@ -595,8 +597,8 @@ constexpr int DD_SMALL = 8192;                              // pages
 constexpr int DD_SMALL_THREADS = 1024;
 constexpr int DD_SMALL_PER = DD_SMALL / DD_SMALL_THREADS;   // pages per thread, blocked
 constexpr int DD_TABLE = 2 * DD_SMALL;                      // hash-table slots
-constexpr unsigned long long DD_EMPTY = ~0ull;
-constexpr size_t DD_SMALL_SMEM = (size_t)DD_TABLE * 8 + (size_t)DD_TABLE * 4 + (size_t)DD_SMALL * 2;
+constexpr uint32_t DD_EMPTY = 0xffffffffu;
+constexpr size_t DD_SMALL_SMEM = (size_t)DD_TABLE * 4 + (size_t)DD_TABLE * 4 + (size_t)DD_SMALL * 2;
 constexpr size_t DD_FINISH_SMEM = (size_t)DD_SMALL * 4 * 4 + (size_t)DD_SMALL * 2 + (size_t)DD_SMALL;
 
 // Region of each page of thread tid's blocked range, from a mark at each
@@ -624,46 +626,55 @@ __device__ void small_regions(const Pages &pg, uint16_t *mark, uint32_t *ws, uin
 }
 
 // Blob ids (canonical data pages numbered in page order), the page table and
-// blob_page, for thread tid's blocked pages.  canon_of(j) gives the
-// canonical page of the thread's j-th page; `bid` is DD_SMALL u32 of shared
-// memory receiving each canonical page's blob id.
+// blob_page.  canon_of(j) gives the canonical page of the thread's j-th
+// (blocked) page.  Shared memory: bid (DD_SMALL u32) receives each
+// canonical page's blob id, cano (DD_SMALL u32) each page's canonical page,
+// regs (DD_SMALL u16) each page's region.  The ids are assigned over the
+// blocked pages; the table rows are then written warp-striped, so that a
+// warp's 16-byte stores are contiguous.
 template <class CanonOf>
 __device__ void small_table(const Pages &pg, const uint8_t *__restrict__ zero, const uint32_t (&reg)[DD_SMALL_PER],
-                            CanonOf canon_of, uint32_t *bid, uint32_t *ws, kc_page *__restrict__ table,
-                            uint32_t *__restrict__ blob_page, uint64_t *__restrict__ misc,
-                            uint64_t *__restrict__ n_blobs_out) {
+                            CanonOf canon_of, uint32_t *bid, uint32_t *cano, uint16_t *regs, uint32_t *ws,
+                            kc_page *__restrict__ table, uint32_t *__restrict__ blob_page,
+                            uint64_t *__restrict__ misc, uint64_t *__restrict__ n_blobs_out) {
     const int tid = threadIdx.x;
     const uint32_t P = (uint32_t)pg.npages;
-    uint8_t z[DD_SMALL_PER];
-    uint32_t c[DD_SMALL_PER];
-    uint32_t nloc = 0;
+    uint32_t flags = 0, nloc = 0;
+    // the thread's 8 zero flags in one load when the array is 8-byte aligned
+    const bool whole = P >= (uint32_t)(tid + 1) * DD_SMALL_PER && (reinterpret_cast<uintptr_t>(zero) & 7) == 0;
+    const uint64_t z8 = whole ? __ldg(reinterpret_cast<const unsigned long long *>(zero) + tid) : 0ull;
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
         const uint32_t p = tid * DD_SMALL_PER + j;
-        z[j] = p < P ? zero[p] : (uint8_t)KC_PAGE_ZERO;
-        c[j] = canon_of(j);
-        nloc += (p < P && z[j] == KC_PAGE_DATA && c[j] == p);
+        const uint8_t z = whole ? (uint8_t)(z8 >> (8 * j)) : (p < P ? zero[p] : (uint8_t)KC_PAGE_ZERO);
+        const uint32_t c = canon_of(j);
+        if (p < P) {
+            cano[p] = c;
+            regs[p] = (uint16_t)reg[j];
+        }
+        const bool f = p < P && z == KC_PAGE_DATA && c == p;
+        flags |= (uint32_t)f << j;
+        nloc += f;
     }
     uint32_t nb = 0;
     uint32_t o = block_excl_sum(nloc, ws, &nb);
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
-        const uint32_t p = tid * DD_SMALL_PER + j;
-        if (p < P && z[j] == KC_PAGE_DATA && c[j] == p) {
+        if ((flags >> j) & 1) {
+            const uint32_t p = tid * DD_SMALL_PER + j;
             bid[p] = o;
             blob_page[o] = p;
             ++o;
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < DD_SMALL_PER; ++j) {
-        const uint32_t p = tid * DD_SMALL_PER + j;
-        if (p >= P) continue;
+    for (uint32_t p = tid; p < P; p += blockDim.x) {
+        const uint8_t z = zero[p];
+        const uint32_t r = regs[p];
         kc_page row;
-        row.va_offset = (p - pg.regions[reg[j]].first) << pg.log2page;
-        row.alloc_id = reg[j];
-        row.blob = z[j] == KC_PAGE_ZERO ? KC_BLOB_ZERO : z[j] == KC_PAGE_LOST ? KC_BLOB_LOST : bid[c[j]];
+        row.va_offset = (p - __ldg(&pg.regions[r].first)) << pg.log2page;
+        row.alloc_id = r;
+        row.blob = z == KC_PAGE_ZERO ? KC_BLOB_ZERO : z == KC_PAGE_LOST ? KC_BLOB_LOST : bid[cano[p]];
         table[p] = row;
     }
     if (tid == 0) {
@@ -672,8 +683,8 @@ __device__ void small_table(const Pages &pg, const uint8_t *__restrict__ zero, c
     }
 }
 
-__device__ __forceinline__ uint32_t dd_slot(uint64_t h) {
-    return (uint32_t)(h ^ (h >> 29) ^ (h >> 47)) & (DD_TABLE - 1);
+__device__ __forceinline__ uint32_t dd_slot(uint32_t k) {
+    return (k ^ (k >> 14) ^ (k >> 28)) & (DD_TABLE - 1);
 }
 
 __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
@@ -681,11 +692,11 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     uint32_t *__restrict__ rep_out, uint32_t *__restrict__ dups, uint32_t *__restrict__ neq,
     kc_page *__restrict__ table, uint32_t *__restrict__ blob_page, uint64_t *__restrict__ n_blobs_out) {
     extern __shared__ __align__(16) uint8_t sm[];
-    unsigned long long *tkey = reinterpret_cast<unsigned long long *>(sm);   // [DD_TABLE]
-    uint32_t *tval = reinterpret_cast<uint32_t *>(tkey + DD_TABLE);          // [DD_TABLE]
+    uint32_t *tkey = reinterpret_cast<uint32_t *>(sm);                       // [DD_TABLE] low 32 hash bits
+    uint32_t *tval = tkey + DD_TABLE;                                        // [DD_TABLE]
     uint16_t *mark = reinterpret_cast<uint16_t *>(tval + DD_TABLE);          // [DD_SMALL]
     __shared__ uint32_t ws[33];
-    __shared__ uint32_t empty_min;   // smallest data page whose hash equals the empty-slot marker
+    __shared__ uint32_t empty_min;   // smallest data page whose key equals the empty-slot marker
     const int tid = threadIdx.x;
     const uint32_t P = (uint32_t)pg.npages;
 
@@ -697,15 +708,26 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     uint32_t reg[DD_SMALL_PER];
     small_regions(pg, mark, ws, reg);   // (its barriers also order the initialisation above)
 
-    // insert: key = hash, value = smallest page id with it
-    uint64_t h[DD_SMALL_PER];
+    // insert: key = low 32 hash bits, value = smallest page id with it
+    uint32_t h[DD_SMALL_PER];
     uint32_t isdata = 0;
+    uint8_t zf[DD_SMALL_PER];
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {   // all loads first: one memory round trip
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        zf[j] = p < P ? __ldg(zero + p) : (uint8_t)KC_PAGE_ZERO;
+        h[j] = p < P ? (uint32_t)__ldg(hash + p) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) isdata |= (uint32_t)(zf[j] == KC_PAGE_DATA) << j;
+    // first insertion attempt of every page at once; a taken slot (another
+    // key) continues along the probe chain
+    uint32_t prev[DD_SMALL_PER];
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
-        const uint32_t p = tid * DD_SMALL_PER + j;
-        const bool d = p < P && zero[p] == KC_PAGE_DATA;
-        isdata |= (uint32_t)d << j;
-        h[j] = d ? hash[p] : 0;
+        prev[j] = DD_EMPTY;
+        if (((isdata >> j) & 1) && h[j] != DD_EMPTY)
+            prev[j] = atomicCAS(&tkey[dd_slot(h[j])], DD_EMPTY, h[j]);
     }
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
@@ -715,18 +737,26 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
             atomicMin(&empty_min, p);
             continue;
         }
-        // at most DD_SMALL keys in DD_TABLE slots: a free or matching slot is always found
-        for (uint32_t s = dd_slot(h[j]), k = 0; k < DD_TABLE; s = (s + 1) & (DD_TABLE - 1), ++k) {
-            const unsigned long long prev = atomicCAS(&tkey[s], DD_EMPTY, (unsigned long long)h[j]);
-            if (prev == DD_EMPTY || prev == h[j]) {
-                atomicMin(&tval[s], p);
-                break;
+        uint32_t s = dd_slot(h[j]);
+        if (prev[j] != DD_EMPTY && prev[j] != h[j]) {
+            // at most DD_SMALL keys in DD_TABLE slots: a free or matching slot is always found
+            for (uint32_t k = 1; k < DD_TABLE; ++k) {
+                s = (s + 1) & (DD_TABLE - 1);
+                const uint32_t q = atomicCAS(&tkey[s], DD_EMPTY, h[j]);
+                if (q == DD_EMPTY || q == h[j]) break;
             }
         }
+        atomicMin(&tval[s], p);
     }
     __syncthreads();
-    // look up each data page's representative
-    uint32_t rep[DD_SMALL_PER];
+    // look up each data page's representative: the first probe of every
+    // page is issued at once, the rest of a probe chain only on a miss
+    uint32_t rep[DD_SMALL_PER], slot[DD_SMALL_PER], k0[DD_SMALL_PER];
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        slot[j] = dd_slot(h[j]);
+        k0[j] = tkey[slot[j]];
+    }
     uint32_t nd = 0;
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
@@ -735,8 +765,10 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
         if (!((isdata >> j) & 1)) continue;
         if (h[j] == DD_EMPTY) {
             rep[j] = empty_min;
+        } else if (k0[j] == h[j]) {
+            rep[j] = tval[slot[j]];
         } else {
-            for (uint32_t s = dd_slot(h[j]), k = 0; k < DD_TABLE; s = (s + 1) & (DD_TABLE - 1), ++k) {
+            for (uint32_t s = (slot[j] + 1) & (DD_TABLE - 1), k = 1; k < DD_TABLE; s = (s + 1) & (DD_TABLE - 1), ++k) {
                 if (tkey[s] == h[j]) {
                     rep[j] = tval[s];
                     break;
@@ -748,10 +780,12 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     uint32_t ndup = 0;
     uint32_t o = block_excl_sum(nd, ws, &ndup);
     if (ndup == 0) {
-        // no two data pages share a hash: every data page is canonical
-        uint32_t *bid = tval;   // the table is no longer needed
-        small_table(pg, zero, reg, [&](int j) { return (uint32_t)(tid * DD_SMALL_PER + j); }, bid, ws, table,
-                    blob_page, misc, n_blobs_out);
+        // no two data pages share a hash: every data page is canonical (the
+        // hash table's memory is reused: it is no longer needed)
+        uint32_t *bid = tval;
+        uint32_t *cano = tkey;
+        small_table(pg, zero, reg, [&](int j) { return (uint32_t)(tid * DD_SMALL_PER + j); }, bid, cano, mark, ws,
+                    table, blob_page, misc, n_blobs_out);
         if (tid == 0) {
             misc[0] = P;
             misc[2] = 0;
@@ -870,7 +904,8 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_finish_kernel(
         }
         __syncthreads();
     }
-    small_table(pg, zero, reg, [&](int j) { return c[j]; }, order, ws, table, blob_page, misc, n_blobs_out);
+    small_table(pg, zero, reg, [&](int j) { return c[j]; }, order, seg, mark, ws, table, blob_page, misc,
+                n_blobs_out);
 }
 
 // ---- 6. pack ----------------------------------------------------------------------
