@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--batched-jobs", type=int, default=4096)
     ap.add_argument("--no-served", action="store_true", help="skip the served-form section")
+    ap.add_argument("--no-moe", action="store_true", help="skip the 30 GiB MoE-pool section")
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--served-rate", type=float, default=50.0)
     return ap.parse_args()
@@ -447,6 +448,8 @@ def run_kc(args):
         "gpu_launches": launches,
         "clocks": sampler.summary(t_wall0, t_wall1),
     }
+    if not args.no_moe:
+        line["moe"] = run_moe_section(args, device, peak)
     if not args.no_batched:
         line["batched"] = run_batched_section(args, device, peak)
     if not args.no_served:
@@ -548,6 +551,83 @@ def run_batched_section(args, device, peak):
     del pb, pp, js, g
     torch.cuda.empty_cache()
     return out
+
+
+def run_moe_section(args, device, peak):
+    """The 30 GiB MoE weight pool (64 experts x 24 layers x 20 MiB of bf16,
+    2% duplicate pages, an int64 array of the 1536 expert pointers), 2 MiB
+    pages: each operation timed on its own with CUDA events (inputs far
+    larger than L2), plus the bf16 [4096, 7168] comparison pairs."""
+    import torch
+    from paper_2605_03208_gb300 import kc
+    from paper_2605_03208_gb300 import workloads as W
+
+    free, _ = torch.cuda.mem_get_info()
+    if free < 75 * W.GiB:
+        return {"skipped": f"needs ~75 GiB free device memory, {free / W.GiB:.0f} GiB free"}
+    t0 = time.time()
+    snap, dev = W.moe_snapshot(args.seed, device=device)
+    pairs = W.moe_pairs(args.seed, device=device)
+    t_gen = time.time() - t0
+    pool, ptrs = dev
+    S = snap.page_bytes
+    ctx = kc.Context(torch.cuda.current_device())
+    b = kc.bufs([(pool.data_ptr(), pool.numel(), kc.BF16, 0), (ptrs.data_ptr(), ptrs.numel() * 8, kc.RAW, 0)])
+    P = kc.page_count(b, S)
+    N = pool.numel() + ptrs.numel() * 8
+    win = W.default_window(snap.bases, snap.sizes)
+    mk = lambda n, dt=torch.uint8: torch.empty(n, dtype=dt, device=device)  # noqa: E731
+    h, z, pf = mk(P, torch.int64), mk(P), mk(3, torch.int64)
+    cap = 1 << 16
+    hits, counts = mk(cap * 24), torch.zeros(2, dtype=torch.int64, device=device)
+    table, nb = mk(P * 16), torch.zeros(1, dtype=torch.int64, device=device)
+    arena = mk(P * S)
+    gb = kc.bufs([(g.data_ptr(), g.numel() * 2, kc.BF16, 0) for g, _, _ in pairs])
+    wb = kc.bufs([(w.data_ptr(), w.numel() * 2, kc.BF16, 0) for _, w, _ in pairs])
+    rec = mk(len(pairs) * 64)
+    C = sum(g.numel() * 2 * 2 for g, _, _ in pairs)
+    st = torch.cuda.current_stream()
+    ops = {
+        "scan": lambda: ctx.scan(b, S, h, z, pf, win[0], win[1], hits, cap, counts, st),
+        "dedup": lambda: ctx.dedup(b, S, h, z, table, arena, P * S, nb, st),
+        "restore": lambda: ctx.restore(b, S, table, P, arena, P * S, st),
+        "compare": lambda: ctx.compare(gb, wb, 0.0, 0.0, rec, st),
+    }
+    reps = {"scan": 5, "dedup": 3, "restore": 3, "compare": 20}
+    out = {}
+    for op in ("scan", "dedup", "restore", "compare"):
+        ops[op]()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps[op]):
+            ops[op]()
+        e1.record(st)
+        e1.synchronize()
+        out[op] = e0.elapsed_time(e1) / reps[op]
+    if ctx.sync(st) != kc.OK:
+        raise RuntimeError("MoE section: device status not OK")
+    cnt = counts.cpu().numpy().view(np.uint64)
+    n_blobs = int(nb.cpu().numpy().view(np.uint64)[0])
+    tbl = table.cpu().numpy().view(kc.PAGE_DTYPE)
+    canon_pages = np.unique(tbl["blob"][tbl["blob"] < 0xFFFFFFFE], return_index=True)[1]
+    U = 0
+    for p in canon_pages.tolist():
+        a, off = int(tbl["alloc_id"][p]), int(tbl["va_offset"][p])
+        U += min(S, int(snap.sizes[a]) - off)
+    ab = {"scan": N + 9 * P, "dedup": 2 * U, "restore": U + N, "compare": C + 64 * len(pairs)}
+    res = {op: {"ms": out[op], "GB/s": ab[op] / (out[op] / 1000) / 1e9,
+                "frac": ab[op] / (out[op] / 1000) / 1e9 / peak, "algorithmic_bytes": ab[op]} for op in out}
+    summary = {
+        "workload": snap.name + ", int64 pointer array of 1536 expert bases, 2 MiB pages; bf16 [4096,7168] x 2 pairs",
+        "snapshot_bytes": N, "pages": P, "unique_bytes": U, "blobs": n_blobs,
+        "census_inside": int(cnt[0]), "census_outside": int(cnt[1]), "gen_s": round(t_gen, 2),
+        "ops": res, "timing": "CUDA events around each call, repeated back to back; inputs 30 GiB > L2",
+    }
+    ctx.close()
+    del pool, ptrs, dev, arena, pairs
+    torch.cuda.empty_cache()
+    return summary
 
 
 def run_served_section(args, device):

@@ -10,6 +10,15 @@
 // to double, and the error values are one IEEE operation each (__dsub_rn,
 // __ddiv_rn, __dmul_rn, __dadd_rn: no FMA contraction), hence identical to
 // any other correctly rounded evaluation.
+//
+// Differing elements are rare and scattered, so evaluating each where it is
+// found would run the FP64 sequence once per element with one lane active;
+// on this part a warp's FP64 instruction costs the same whatever its active
+// lanes.  They are queued instead (index and both bit patterns, in shared
+// memory) and the queue is evaluated at the end of the tile with every lane
+// busy.  What is accumulated -- counts, the smallest index, maxima -- does
+// not depend on the order, so the results are unchanged.  An element that
+// finds the queue full is evaluated where it is.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -68,6 +77,52 @@ __device__ __forceinline__ void cmp_slow(uint32_t gb, uint32_t wb, unsigned long
     }
 }
 
+// Synchronisation of the threads sharing a tile.
+struct CtaSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+// Queue of elements whose bits differ (shared memory).
+struct SlowItem {
+    unsigned long long idx;
+    uint32_t g, w;
+};
+struct SlowQ {
+    SlowItem *items;   // null: no queue, evaluate in place
+    uint32_t *count;
+    uint32_t cap;
+};
+
+template <int DT>
+__device__ __forceinline__ void cmp_defer(const SlowQ &q, uint32_t gb, uint32_t wb, unsigned long long idx,
+                                          double atol, double rtol, CmpAcc &acc) {
+    if (q.items) {
+        const uint32_t pos = atomicAdd(q.count, 1u);
+        if (pos < q.cap) {
+            q.items[pos] = SlowItem{idx, gb, wb};
+            return;
+        }
+    }
+    cmp_slow<DT>(gb, wb, idx, atol, rtol, acc);
+}
+
+// Evaluate the queued elements with all nthr threads; the caller
+// synchronises its threads before (the queue is complete) and after (the
+// queue may be reset).
+template <int DT>
+__device__ __forceinline__ void cmp_drain(const SlowQ &q, double atol, double rtol, CmpAcc &acc, uint32_t tid,
+                                          uint32_t nthr) {
+    if (!q.items) return;
+    const uint32_t n = *q.count < q.cap ? *q.count : q.cap;
+    for (uint32_t i = tid; i < n; i += nthr) {
+        const SlowItem it = q.items[i];
+        cmp_slow<DT>(it.g, it.w, it.idx, atol, rtol, acc);
+    }
+}
+
 template <int DT>
 __host__ __device__ constexpr int esize() {
     return DT == KC_F32 || DT == KC_I32 ? 4 : DT == KC_F16 || DT == KC_BF16 ? 2 : 1;
@@ -91,7 +146,7 @@ __device__ __forceinline__ uint32_t word_nans(uint32_t w) {
 
 template <int DT>
 __device__ __forceinline__ void cmp_word(uint32_t g, uint32_t w, unsigned long long first_elem,
-                                         double atol, double rtol, CmpAcc &acc) {
+                                         double atol, double rtol, CmpAcc &acc, const SlowQ &q) {
     constexpr int per = 4 / esize<DT>();
     if (g == w) {
         const uint32_t n = word_nans<DT>(g);
@@ -107,14 +162,14 @@ __device__ __forceinline__ void cmp_word(uint32_t g, uint32_t w, unsigned long l
             acc.nan_g += n;
             acc.nan_w += n;
         } else {
-            cmp_slow<DT>(ge, we, first_elem + j, atol, rtol, acc);
+            cmp_defer<DT>(q, ge, we, first_elem + j, atol, rtol, acc);
         }
     }
 }
 
 template <int DT>
 __device__ __forceinline__ void cmp_vec(uint4 g, uint4 w, unsigned long long first_elem, double atol,
-                                        double rtol, CmpAcc &acc) {
+                                        double rtol, CmpAcc &acc, const SlowQ &q) {
     constexpr int per = 4 / esize<DT>();
     if (g.x == w.x && g.y == w.y && g.z == w.z && g.w == w.w) {
         if (DT == KC_F32 || DT == KC_F16 || DT == KC_BF16) {
@@ -125,18 +180,19 @@ __device__ __forceinline__ void cmp_vec(uint4 g, uint4 w, unsigned long long fir
         }
         return;
     }
-    cmp_word<DT>(g.x, w.x, first_elem, atol, rtol, acc);
-    cmp_word<DT>(g.y, w.y, first_elem + per, atol, rtol, acc);
-    cmp_word<DT>(g.z, w.z, first_elem + 2 * per, atol, rtol, acc);
-    cmp_word<DT>(g.w, w.w, first_elem + 3 * per, atol, rtol, acc);
+    cmp_word<DT>(g.x, w.x, first_elem, atol, rtol, acc, q);
+    cmp_word<DT>(g.y, w.y, first_elem + per, atol, rtol, acc, q);
+    cmp_word<DT>(g.z, w.z, first_elem + 2 * per, atol, rtol, acc, q);
+    cmp_word<DT>(g.w, w.w, first_elem + 3 * per, atol, rtol, acc, q);
 }
 
 // One tile of one pair, shared by `nthr` threads (tid = 0 .. nthr-1); each
 // thread keeps U 16-byte loads of each buffer in flight (a CTA-wide tile
 // needs few, a warp alone on a tile needs more to cover the DRAM latency).
-template <int DT, int U>
+// sync() synchronises the nthr threads; the tile ends by draining the queue.
+template <int DT, int U, class Sync>
 __device__ void cmp_tile(const CmpPair &pr, uint64_t tile_in_pair, double atol, double rtol, CmpAcc &acc,
-                         uint32_t tid, uint32_t nthr) {
+                         uint32_t tid, uint32_t nthr, const SlowQ &q, Sync sync) {
     constexpr int ES = esize<DT>();
     const uint64_t nbytes = pr.nelem * ES;
     const uint64_t t0 = tile_in_pair * CMP_TILE_BYTES;
@@ -154,11 +210,11 @@ __device__ void cmp_tile(const CmpPair &pr, uint64_t tile_in_pair, double atol, 
         }
 #pragma unroll
         for (int j = 0; j < U; ++j)
-            cmp_vec<DT>(gv[j], wv[j], (t0 + 16 * (v + j * nthr)) / ES, atol, rtol, acc);
+            cmp_vec<DT>(gv[j], wv[j], (t0 + 16 * (v + j * nthr)) / ES, atol, rtol, acc, q);
     }
     for (; v < nvec; v += nthr) {
         uint4 gv = ldg_stream(g + 16 * v), wv = ldg_stream(w + 16 * v);
-        cmp_vec<DT>(gv, wv, (t0 + 16 * v) / ES, atol, rtol, acc);
+        cmp_vec<DT>(gv, wv, (t0 + 16 * v) / ES, atol, rtol, acc, q);
     }
     // ragged end of the pair: fewer than 16 bytes, element by element
     const uint64_t tail0 = nvec << 4;
@@ -173,9 +229,34 @@ __device__ void cmp_tile(const CmpPair &pr, uint64_t tile_in_pair, double atol, 
             acc.nan_g += n;
             acc.nan_w += n;
         } else {
-            cmp_slow<DT>(gb, wb, (t0 + b) / ES, atol, rtol, acc);
+            cmp_defer<DT>(q, gb, wb, (t0 + b) / ES, atol, rtol, acc);
         }
     }
+    (void)sync;
+}
+
+// Drain the queue (elements of the pair of dtype dt) if it holds at least
+// `min_items`: all nthr threads call it; returns with the queue empty or
+// below that mark.  A queue is drained at the latest when the pair changes
+// and when the caller's work ends (min_items = 1).
+template <class Sync>
+__device__ __forceinline__ void cmp_drain_any(int dt, const SlowQ &q, uint32_t min_items, double atol, double rtol,
+                                              CmpAcc &acc, uint32_t tid, uint32_t nthr, Sync sync) {
+    if (!q.items) return;
+    sync();
+    const uint32_t n = *q.count;
+    sync();                      // every thread has read the count before any adds to it again
+    if (n < min_items) return;   // uniform: every thread read the same count
+    switch (dt) {
+    case KC_F32: cmp_drain<KC_F32>(q, atol, rtol, acc, tid, nthr); break;
+    case KC_F16: cmp_drain<KC_F16>(q, atol, rtol, acc, tid, nthr); break;
+    case KC_BF16: cmp_drain<KC_BF16>(q, atol, rtol, acc, tid, nthr); break;
+    case KC_I32: cmp_drain<KC_I32>(q, atol, rtol, acc, tid, nthr); break;
+    default: cmp_drain<KC_U8>(q, atol, rtol, acc, tid, nthr); break;
+    }
+    sync();
+    if (tid == 0) *q.count = 0;
+    sync();
 }
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
@@ -210,15 +291,15 @@ __device__ __forceinline__ void cmp_warp_flush(const CmpAcc &acc, kc_cmp_result 
 }
 
 // Comparison of one tile by `nthr` threads, dispatched on the pair's dtype.
-template <int U>
+template <int U, class Sync>
 __device__ __forceinline__ void cmp_tile_any(const CmpPair &pr, uint64_t tile, double atol, double rtol, CmpAcc &acc,
-                                             uint32_t tid, uint32_t nthr) {
+                                             uint32_t tid, uint32_t nthr, const SlowQ &q, Sync sync) {
     switch (pr.dtype) {
-    case KC_F32: cmp_tile<KC_F32, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    case KC_F16: cmp_tile<KC_F16, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    case KC_BF16: cmp_tile<KC_BF16, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    case KC_I32: cmp_tile<KC_I32, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
-    default: cmp_tile<KC_U8, U>(pr, tile, atol, rtol, acc, tid, nthr); break;
+    case KC_F32: cmp_tile<KC_F32, U>(pr, tile, atol, rtol, acc, tid, nthr, q, sync); break;
+    case KC_F16: cmp_tile<KC_F16, U>(pr, tile, atol, rtol, acc, tid, nthr, q, sync); break;
+    case KC_BF16: cmp_tile<KC_BF16, U>(pr, tile, atol, rtol, acc, tid, nthr, q, sync); break;
+    case KC_I32: cmp_tile<KC_I32, U>(pr, tile, atol, rtol, acc, tid, nthr, q, sync); break;
+    default: cmp_tile<KC_U8, U>(pr, tile, atol, rtol, acc, tid, nthr, q, sync); break;
     }
 }
 

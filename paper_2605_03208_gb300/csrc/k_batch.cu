@@ -108,8 +108,16 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchJob *__restrict__
             CmpAcc acc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0};
             const uint64_t tiles = (J.bytes + CMP_TILE_BYTES - 1) / CMP_TILE_BYTES;
             const uint64_t t0 = (R.first + k) * (BATCH_CMP_ITEM_BYTES / CMP_TILE_BYTES);
+            // the warp's digest ring is idle during a comparison item: it
+            // holds the queue of differing elements (count, then items)
+            const size_t ring_bytes = (size_t)stages * BATCH_PPW * ((size_t)chunk + 32);
+            const SlowQ q{reinterpret_cast<SlowItem *>(ring + 16), reinterpret_cast<uint32_t *>(ring),
+                          (uint32_t)((ring_bytes - 16) / sizeof(SlowItem))};
+            if (lane == 0) *q.count = 0;
+            __syncwarp();
             for (uint64_t tile = t0; tile < t0 + BATCH_CMP_ITEM_BYTES / CMP_TILE_BYTES && tile < tiles; ++tile)
-                cmp_tile_any<6>(pr, tile, atol, rtol, acc, lane, 32);
+                cmp_tile_any<6>(pr, tile, atol, rtol, acc, lane, 32, q, WarpSync{});
+            cmp_drain_any(pr.dtype, q, 1, atol, rtol, acc, lane, 32, WarpSync{});
             cmp_warp_flush(acc, J.cmp);
         }
         if (J.done) batch_item_done(J, left + R.job);

@@ -17,6 +17,7 @@
 namespace kc {
 
 constexpr int CMP_THREADS = 256;
+constexpr uint32_t CMP_QCAP = 1024;   // queued differing elements per CTA (16 KB)
 
 __global__ void cmp_init_kernel(const CmpPair *__restrict__ pairs, int npairs, kc_cmp_result *__restrict__ out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,13 +73,18 @@ __device__ void cmp_flush(CmpAcc &acc, kc_cmp_result *o, unsigned long long (*re
 // Each CTA takes a contiguous range of tiles, so consecutive tiles mostly
 // belong to the same pair and a CTA merges into a pair's record once per
 // pair it touches, not once per tile.
-__global__ void __launch_bounds__(CMP_THREADS) cmp_kernel(const CmpPair *__restrict__ pairs, int npairs,
+__global__ void __launch_bounds__(CMP_THREADS, 3) cmp_kernel(const CmpPair *__restrict__ pairs, int npairs,
                                                           uint64_t ntiles, double atol, double rtol,
                                                           kc_cmp_result *__restrict__ out) {
     __shared__ unsigned long long red[7][CMP_THREADS / 32];
+    __shared__ SlowItem qitems[CMP_QCAP];
+    __shared__ uint32_t qcount;
     const uint64_t t0 = ntiles * blockIdx.x / gridDim.x;
     const uint64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
     if (t0 >= t1) return;
+    if (threadIdx.x == 0) qcount = 0;
+    __syncthreads();
+    const SlowQ q{qitems, &qcount, CMP_QCAP};
     // pair owning t0: last pair whose first tile <= t0
     int lo = 0, hi = npairs - 1;
     while (lo < hi) {
@@ -92,14 +98,19 @@ __global__ void __launch_bounds__(CMP_THREADS) cmp_kernel(const CmpPair *__restr
     for (uint64_t tile = t0; tile < t1; ++tile) {
         bool moved = false;
         while (k + 1 < npairs && pairs[k + 1].tile_first <= tile) {
-            if (!moved) cmp_flush(acc, &out[k], red);
+            if (!moved) {
+                cmp_drain_any(pr.dtype, q, 1, atol, rtol, acc, threadIdx.x, CMP_THREADS, CtaSync{});
+                cmp_flush(acc, &out[k], red);
+            }
             moved = true;
             ++k;
         }
         if (moved) pr = pairs[k];
         if (pr.lost) continue;
-        cmp_tile_any<4>(pr, tile - pr.tile_first, atol, rtol, acc, threadIdx.x, CMP_THREADS);
+        cmp_tile_any<4>(pr, tile - pr.tile_first, atol, rtol, acc, threadIdx.x, CMP_THREADS, q, CtaSync{});
+        cmp_drain_any(pr.dtype, q, CMP_QCAP / 2, atol, rtol, acc, threadIdx.x, CMP_THREADS, CtaSync{});
     }
+    cmp_drain_any(pr.dtype, q, 1, atol, rtol, acc, threadIdx.x, CMP_THREADS, CtaSync{});
     cmp_flush(acc, &out[k], red);
 }
 

@@ -179,6 +179,7 @@ struct BatchRange {        // 32 bytes
     uint32_t kind;         // 0: digest pages, PPW pages per item; 1: comparison items
 };
 constexpr uint32_t BATCH_CMP_ITEM_BYTES = 4 * CMP_TILE_BYTES;   // 64 KiB per comparison item
+static_assert(BATCH_CMP_ITEM_BYTES == KC_BATCH_ITEM_BYTES, "comparison item size");
 cudaError_t launch_batch(const BatchJob *jobs, int njobs, uint32_t *left, const BatchRange *ranges, int nranges,
                          uint64_t nitems, uint32_t page, const DigestShape &shape, double atol, double rtol,
                          uint32_t *ctr, int sms, cudaStream_t st);
