@@ -270,6 +270,10 @@ KC_API kc_status kc_dedup(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t pag
  * the arena (arena_bytes) are skipped and reported as KC_EINVAL by kc_sync.
  * `allocs` gives the restore targets: the captured VAs for a VA-faithful
  * restore, or explicit new bases (a relocation the caller asks for).
+ * d_arena may also be pinned host memory the device can address (e.g. a
+ * snapshot image loaded from disk): the kernel then reads it over the host
+ * link, with no staging copy.  A table whose row p has blob = p restores a
+ * page-slotted image (page p in bytes [p*S, (p+1)*S)).
  */
 KC_API kc_status kc_restore(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page_bytes,
                      const kc_page *d_table, uint64_t n_pages, const uint8_t *d_arena,
