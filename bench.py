@@ -225,9 +225,9 @@ class KcStep:
 # DRAM traffic of one digest_kernel<census> launch on this workload, from the
 # ncu capture summarised in profiles/digest_kernel_llama400.md, valid only for
 # the kernel sources it was taken on (sha1 of each file, first 8 hex digits).
-DIGEST_TRAFFIC = {"bytes": 402_742_016 + 3_481_088,
-                  "sources": {"k_digest.cu": "eac3c08b", "digest_task.cuh": "e56d6bfd",
-                              "kc_device.cuh": "8385f4d8"}}
+DIGEST_TRAFFIC = {"bytes": 402_745_088 + 3_981_056,
+                  "sources": {"k_digest.cu": "29459998", "digest_task.cuh": "411ed35a",
+                              "kc_device.cuh": "d43b1599"}}
 
 
 def digest_traffic():
