@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--batched-jobs", type=int, default=4096)
     ap.add_argument("--no-served", action="store_true", help="skip the served-form section")
     ap.add_argument("--no-moe", action="store_true", help="skip the 30 GiB MoE-pool section")
+    ap.add_argument("--no-snapshot-io", action="store_true", help="skip the save/load-to-disk section")
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--served-rate", type=float, default=50.0)
     return ap.parse_args()
@@ -472,6 +473,8 @@ def run_kc(args):
         "gpu_launches": launches,
         "clocks": sampler.summary(t_wall0, t_wall1),
     }
+    if not args.no_snapshot_io:
+        line["snapshot_io"] = run_snapshot_io_section(ctx, step, snap, dev)
     if not args.no_moe:
         line["moe"] = run_moe_section(args, device, peak)
     if not args.no_batched:
@@ -575,6 +578,33 @@ def run_batched_section(args, device, peak):
     del pb, pp, js, g
     torch.cuda.empty_cache()
     return out
+
+
+def run_snapshot_io_section(ctx, step, snap, dev):
+    """The llama-shaped snapshot saved to a directory (device reduction, the
+    deduplicated arena streamed through pinned buffers to a file) and loaded
+    back at its VAs; the paper streams its snapshots at ~1.7 GB/s (another
+    machine: context only)."""
+    import shutil
+    import tempfile
+    from paper_2605_03208_gb300 import snapshot_io as SIO
+    d = tempfile.mkdtemp(prefix="kc_snapshot_")
+    try:
+        t0 = time.perf_counter()
+        m = SIO.save(ctx, step.b, step.S, d)
+        t_save = time.perf_counter() - t0
+        for t in dev:
+            t.fill_(0xA5)
+        t1 = time.perf_counter()
+        SIO.load(ctx, d)
+        t_load = time.perf_counter() - t1
+        ok = all(np.array_equal(t.cpu().numpy(), r) for t, r in zip(dev, snap.regions))
+        return {"snapshot_bytes": step.N, "arena_bytes": m["sizes"]["arena"], "save_s": t_save, "load_s": t_load,
+                "save_GBps": step.N / t_save / 1e9, "load_GBps": step.N / t_load / 1e9,
+                "arena_stream_GBps": m["timings"]["arena_GBps"], "restored_exactly": bool(ok),
+                "storage": d.rsplit("/", 1)[0] + " (temporary directory on the box)"}
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
 
 
 def run_moe_section(args, device, peak):
