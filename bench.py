@@ -587,6 +587,7 @@ def run_snapshot_io_section(ctx, step, snap, dev):
     machine: context only)."""
     import shutil
     import tempfile
+    import torch
     from paper_2605_03208_gb300 import snapshot_io as SIO
     d = tempfile.mkdtemp(prefix="kc_snapshot_")
     try:
@@ -599,7 +600,22 @@ def run_snapshot_io_section(ctx, step, snap, dev):
         SIO.load(ctx, d)
         t_load = time.perf_counter() - t1
         ok = all(np.array_equal(t.cpu().numpy(), r) for t, r in zip(dev, snap.regions))
-        return {"snapshot_bytes": step.N, "arena_bytes": m["sizes"]["arena"], "save_s": t_save, "load_s": t_load,
+        # multi-iteration replay: the resident deduplicated snapshot re-copied
+        # over the regions before an iteration (kc_restore, device to device)
+        from paper_2605_03208_gb300 import replay as RP
+        res = RP.capture(ctx, step.b, step.S)
+        st = torch.cuda.current_stream()
+        RP.recopy(ctx, res, st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(20):
+            RP.recopy(ctx, res, st)
+        e1.record(st)
+        e1.synchronize()
+        recopy_ms = e0.elapsed_time(e1) / 20
+        del res
+        return {"replay_recopy_ms": recopy_ms, "replay_recopy_GBps": step.N / (recopy_ms / 1000) / 1e9,
+                "snapshot_bytes": step.N, "arena_bytes": m["sizes"]["arena"], "save_s": t_save, "load_s": t_load,
                 "save_GBps": step.N / t_save / 1e9, "load_GBps": step.N / t_load / 1e9,
                 "arena_stream_GBps": m["timings"]["arena_GBps"], "restored_exactly": bool(ok),
                 "storage": d.rsplit("/", 1)[0] + " (temporary directory on the box)"}
