@@ -105,11 +105,11 @@ __device__ __forceinline__ UnitSpan unit_span(const Pages &u, uint64_t unit) {
 constexpr int TAIL_THREADS = 512;
 constexpr int TAIL_WARPS = TAIL_THREADS / 32;
 constexpr int TAIL_CHUNK = 32;     // most pages per chunk (one warp lane each when listing them)
-constexpr int TAIL_STASH = 32;     // hits a warp keeps in shared memory
+constexpr int TAIL_STASH = 128;    // hits a warp keeps in shared memory (48 KB per CTA)
 constexpr unsigned long long LB_AGG = 1ull << 62;      // chunk word: total of the chunk
 constexpr unsigned long long LB_PREFIX = 2ull << 62;   // chunk word: inclusive prefix
 constexpr unsigned long long LB_VALUE = (1ull << 62) - 1;
-constexpr uint32_t LB_SPIN_LIMIT = 1u << 20;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 22;   // polls of ~1 us each: a few seconds at most
 
 // Span of page p of region ri.
 __device__ __forceinline__ UnitSpan page_span(const Pages &u, uint64_t p, int ri) {
@@ -124,10 +124,11 @@ __device__ __forceinline__ UnitSpan page_span(const Pages &u, uint64_t p, int ri
 }
 
 // Exclusive prefix of chunk c: warp 0 reads the words of 256 earlier chunks
-// at a time, 8 consecutive ones per lane (lane l holds the chunks 8l .. 8l+7
-// before the window's start, nearest first), waits (bounded) until each is
-// published, and stops at the nearest inclusive prefix, adding the totals
-// of the chunks between it and c.
+// at a time -- load k of lane l is the chunk at distance 32k + l + 1, so each
+// load instruction covers 32 consecutive words (two cache lines: many chunks
+// poll the same few lines) -- waits (bounded) until each is published, and
+// stops at the nearest inclusive prefix, adding the totals of the chunks
+// between it and c.
 __device__ __forceinline__ unsigned long long lookback(volatile unsigned long long *word, uint64_t c,
                                                        uint32_t *status) {
     const uint32_t lane = lane_id();
@@ -135,52 +136,53 @@ __device__ __forceinline__ unsigned long long lookback(volatile unsigned long lo
     int64_t base = (int64_t)c - 1;
     while (base >= 0) {
         unsigned long long w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = 0;
         uint32_t spins = 0;
-        bool missing;
-        do {
+        bool missing = true;
+        while (true) {
             missing = false;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const int64_t j = base - 8 * (int64_t)lane - k;
-                w[k] = LB_PREFIX;   // before the first chunk: prefix 0
-                if (j >= 0) w[k] = word[j];
-                missing |= (w[k] & ~LB_VALUE) == 0;
+                if ((w[k] & ~LB_VALUE) == 0) {   // not seen published yet
+                    const int64_t j = base - (32 * k + (int64_t)lane);
+                    unsigned long long x = LB_PREFIX;   // before the first chunk: prefix 0
+                    if (j >= 0) x = word[j];
+                    w[k] = x;
+                    missing |= (w[k] & ~LB_VALUE) == 0;
+                }
             }
-            if (__any_sync(0xffffffffu, missing)) {
-                __nanosleep(32);
-                ++spins;
-            }
-        } while (__any_sync(0xffffffffu, missing) && spins < LB_SPIN_LIMIT);
+            if (!__any_sync(0xffffffffu, missing) || ++spins >= LB_SPIN_LIMIT) break;
+        }
         if (__any_sync(0xffffffffu, missing)) {
             if (lane == 0) set_status(status, ST_TIMEOUT);
             break;   // give up: the prefix is wrong, the status says so
         }
-        // this lane: the nearest inclusive prefix among its 8, and the sum up to it
+        // nearest inclusive prefix: the smallest distance 32k + l holding one
+        uint32_t dmin = 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if ((w[k] & LB_PREFIX) && dmin == 0xffffffffu) dmin = 32 * k + lane;
+        dmin = __reduce_min_sync(0xffffffffu, dmin);
         unsigned long long part = 0;
-        bool has = false;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (!has) {
-                part += w[k] & LB_VALUE;
-                has = (w[k] & LB_PREFIX) != 0;
-            }
-        }
-        const uint32_t pm = __ballot_sync(0xffffffffu, has);
-        const uint32_t upto = pm ? (uint32_t)__ffs(pm) - 1 : 31u;
-        unsigned long long v = lane <= upto ? part : 0ull;
+        for (int k = 0; k < 8; ++k)
+            if ((uint32_t)(32 * k) + lane <= dmin) part += w[k] & LB_VALUE;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        prefix += v;
-        if (pm) break;
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        prefix += part;
+        if (dmin != 0xffffffffu) break;
         base -= 256;
     }
     return prefix;
 }
 
 // One warp's run [a, b) of the chunk's flagged-page word sequence: classify
-// (hits to `out`, up to `cap` of them, in word order) and count.
-__device__ __forceinline__ void tail_run(const Pages &u, const CensusArgs &ca, const Range *rg, uint64_t p0,
-                                         const uint32_t *preg, const uint32_t *fpage, const uint64_t *fstart,
+// (hits to `out`, up to `cap` of them, in word order) and count.  fpid /
+// freg: the flagged pages' ids and region index + 1, fstart their word
+// offsets in the sequence.
+__device__ __forceinline__ void tail_run(const Pages &u, const CensusArgs &ca, const Range *rg,
+                                         const uint64_t *fpid, const uint32_t *freg, const uint64_t *fstart,
                                          int nflag, uint64_t a, uint64_t b, kc_hit *out, uint64_t cap,
                                          uint32_t &nin, uint32_t &nout) {
     nin = 0;
@@ -190,8 +192,7 @@ __device__ __forceinline__ void tail_run(const Pages &u, const CensusArgs &ca, c
         if (s1 <= a) continue;
         if (s0 >= b) break;
         const uint64_t wb = (a > s0 ? a : s0) - s0, we = (b < s1 ? b : s1) - s0;
-        const uint64_t p = p0 + fpage[i];
-        const UnitSpan sp = page_span(u, p, (int)preg[fpage[i]] - 1);
+        const UnitSpan sp = page_span(u, fpid[i], (int)freg[i] - 1);
         uint32_t ni = 0, no = 0;
         const uint64_t done = nin + nout;
         warp_census_range(ca, rg, sp.base, wb, we, sp.off, (uint32_t)sp.region, out, done, cap, ni, no);
@@ -200,16 +201,74 @@ __device__ __forceinline__ void tail_run(const Pages &u, const CensusArgs &ca, c
     }
 }
 
+// The flagged pages (page_hits != 0) in page order, for the tail's list
+// mode: one CTA, a block-wide scan per tile of pages.
+constexpr int FLAG_THREADS = 1024;
+constexpr int FLAG_ITEMS = 8;
+
+__global__ void __launch_bounds__(FLAG_THREADS) census_flag_list_kernel(const uint32_t *__restrict__ page_hits,
+                                                                        uint64_t npages, uint32_t *__restrict__ list,
+                                                                        uint32_t *__restrict__ nlist) {
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (uint64_t t0 = 0; t0 < npages; t0 += (uint64_t)FLAG_THREADS * FLAG_ITEMS) {
+        uint32_t f = 0, n = 0;
+#pragma unroll
+        for (int j = 0; j < FLAG_ITEMS; ++j) {
+            const uint64_t p = t0 + (uint64_t)tid * FLAG_ITEMS + j;
+            const bool on = p < npages && page_hits[p] != 0;
+            f |= (uint32_t)on << j;
+            n += on;
+        }
+        uint32_t inc = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) ws[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t x = ws[lane];
+            uint32_t xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += y;
+            }
+            ws[lane] = xi - x;
+        }
+        __syncthreads();
+        uint32_t at = s_base + ws[warp] + inc - n;
+#pragma unroll
+        for (int j = 0; j < FLAG_ITEMS; ++j)
+            if ((f >> j) & 1) list[at++] = (uint32_t)(t0 + (uint64_t)tid * FLAG_ITEMS + j);
+        __syncthreads();
+        if (tid == FLAG_THREADS - 1) s_base = at;
+        __syncthreads();
+    }
+    if (tid == 0) *nlist = s_base;
+}
+
+// List mode (list != null): chunk c holds entries [c * cpages, ...) of the
+// page-ordered list of flagged pages (*nlist of them), so a chunk's work is
+// bounded by cpages pages however the flagged pages cluster.
 __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, CensusArgs ca,
                                                                     const uint32_t *__restrict__ page_hits,
                                                                     unsigned long long *__restrict__ tail,
                                                                     uint64_t nchunks, uint32_t cpages,
+                                                                    const uint32_t *__restrict__ list,
+                                                                    const uint32_t *__restrict__ nlist,
                                                                     kc_hit *__restrict__ hits, uint64_t cap,
                                                                     uint64_t *__restrict__ counts,
                                                                     uint32_t *__restrict__ status) {
     __shared__ Range srg[SMEM_RANGES];
     __shared__ kc_hit stash[TAIL_WARPS][TAIL_STASH];
-    __shared__ uint32_t preg[TAIL_CHUNK], fpage[TAIL_CHUNK];
+    __shared__ uint32_t freg[TAIL_CHUNK];
+    __shared__ uint64_t fpid[TAIL_CHUNK];
     __shared__ uint64_t fstart[TAIL_CHUNK + 1];
     __shared__ uint32_t wn[TAIL_WARPS], win_s[TAIL_WARPS], wout_s[TAIL_WARPS];
     __shared__ int s_nflag;
@@ -219,17 +278,23 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
     const uint32_t lane = lane_id();
     unsigned long long *ticket = tail;
     volatile unsigned long long *word = tail + 1;
+    const uint64_t nentries = list ? (uint64_t)*nlist : u.npages;
+    if (list) {   // spread the flagged pages over the grid: at most TAIL_CHUNK per chunk
+        uint64_t cp = (nentries + gridDim.x - 1) / gridDim.x;
+        cpages = (uint32_t)(cp < 1 ? 1 : cp > (uint64_t)TAIL_CHUNK ? TAIL_CHUNK : cp);
+        nchunks = (nentries + cpages - 1) / cpages;
+    }
     while (true) {
         if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1ull);
         __syncthreads();
         const uint64_t c = s_chunk;
         if (c >= nchunks) break;
-        const uint64_t p0 = c * cpages;
-        const uint64_t p1 = p0 + cpages < u.npages ? p0 + cpages : u.npages;
+        const uint64_t e0 = c * cpages;
+        const uint64_t e1 = e0 + cpages < nentries ? e0 + cpages : nentries;
         if (warp == 0) {   // the flagged pages and their word offsets in the chunk's sequence
-            const uint64_t p = p0 + lane;
-            const uint32_t r = p < p1 ? page_hits[p] : 0u;
-            preg[lane] = r;
+            const uint64_t e = e0 + lane;
+            const uint64_t p = e < e1 ? (list ? (uint64_t)list[e] : e) : 0;
+            const uint32_t r = e < e1 ? page_hits[p] : 0u;
             const uint64_t nw = r ? page_span(u, p, (int)r - 1).nwords : 0;
             const uint32_t fm = __ballot_sync(0xffffffffu, r != 0);
             uint64_t inc = nw;
@@ -240,7 +305,8 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
             }
             if (r) {
                 const int slot = __popc(fm & lanemask_lt());
-                fpage[slot] = lane;
+                fpid[slot] = p;
+                freg[slot] = r;
                 fstart[slot] = inc - nw;
             }
             if (lane == 31) {
@@ -256,7 +322,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
             const uint64_t T = fstart[nflag];
             const uint64_t a = T * warp / TAIL_WARPS, b = T * (warp + 1) / TAIL_WARPS;
             uint32_t nin, nout;
-            tail_run(u, ca, rg, p0, preg, fpage, fstart, nflag, a, b, stash[warp], TAIL_STASH, nin, nout);
+            tail_run(u, ca, rg, fpid, freg, fstart, nflag, a, b, stash[warp], TAIL_STASH, nin, nout);
             if (lane == 0) {
                 wn[warp] = nin + nout;
                 win_s[warp] = nin;
@@ -306,7 +372,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
                 const uint64_t T = fstart[nflag];
                 const uint64_t a = T * warp / TAIL_WARPS, b = T * (warp + 1) / TAIL_WARPS;
                 uint32_t nin, nout;
-                tail_run(u, ca, rg, p0, preg, fpage, fstart, nflag, a, b, hits + before, cap > before ? cap - before : 0,
+                tail_run(u, ca, rg, fpid, freg, fstart, nflag, a, b, hits + before, cap > before ? cap - before : 0,
                          nin, nout);
             }
         }
@@ -314,8 +380,8 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
     }
 }
 
-// Pages per chunk: enough chunks for every resident CTA to take one, as
-// few as 8 pages and at most TAIL_CHUNK.
+// Pages per chunk (page mode): enough chunks for every resident CTA to take
+// one, as few as 8 pages and at most TAIL_CHUNK.
 static uint32_t tail_chunk_pages(uint64_t npages, int sms) {
     const uint64_t ctas = (uint64_t)sms * 2;   // resident CTAs (2 per SM by registers)
     uint64_t cp = (npages + ctas - 1) / ctas;
@@ -324,22 +390,37 @@ static uint32_t tail_chunk_pages(uint64_t npages, int sms) {
     return (uint32_t)cp;
 }
 
-uint64_t census_tail_chunks(uint64_t npages, int sms) {
+// Snapshots of up to this many pages use list mode (the flagged pages listed
+// in page order by one CTA first).
+constexpr uint64_t TAIL_LIST_MAX = 1ull << 16;
+
+uint64_t census_tail_words(uint64_t npages, int sms) {
+    if (npages <= TAIL_LIST_MAX) return 1 + npages;
     const uint32_t cp = tail_chunk_pages(npages, sms);
-    return (npages + cp - 1) / cp;
+    return 1 + (npages + cp - 1) / cp;
 }
 
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
-                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, int sms,
-                               cudaStream_t st) {
-    const uint32_t cp = tail_chunk_pages(pg.npages, sms);
-    const uint64_t nchunks = (pg.npages + cp - 1) / cp;
-    if (nchunks == 0) return cudaSuccess;
-    uint64_t blocks = nchunks;
+                               uint32_t *list, kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status,
+                               int sms, cudaStream_t st) {
+    if (pg.npages == 0) return cudaSuccess;
     const uint64_t maxb = (uint64_t)sms * 2;
-    if (blocks > maxb) blocks = maxb;
-    census_tail_kernel<<<(unsigned)blocks, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, nchunks, cp,
-                                                                  cap ? hits : nullptr, cap, counts, status);
+    if (pg.npages <= TAIL_LIST_MAX) {
+        uint32_t *nlist = list + pg.npages;
+        census_flag_list_kernel<<<1, FLAG_THREADS, 0, st>>>(page_hits, pg.npages, list, nlist);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        census_tail_kernel<<<(unsigned)maxb, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, pg.npages, 1, list, nlist,
+                                                                    cap ? hits : nullptr, cap, counts, status);
+    } else {
+        const uint32_t cp = tail_chunk_pages(pg.npages, sms);
+        const uint64_t nchunks = (pg.npages + cp - 1) / cp;
+        const uint64_t blocks = nchunks < maxb ? nchunks : maxb;
+        census_tail_kernel<<<(unsigned)blocks, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, nchunks, cp, nullptr,
+                                                                      nullptr, cap ? hits : nullptr, cap, counts,
+                                                                      status);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -542,5 +623,6 @@ cudaError_t launch_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint6
     count_launches(1);
     return cudaGetLastError();
 }
+
 
 }  // namespace kc

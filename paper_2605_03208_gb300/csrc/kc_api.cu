@@ -617,14 +617,17 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
     const DigestShape shape = pick_shape(c, page_bytes, P);
     uint32_t *page_hits = nullptr;
     unsigned long long *tail = nullptr;
+    uint32_t *list = nullptr;
     DigestAux aux;
     if (census) {
-        // page_hits[P] | census tail: ticket + one word per chunk of pages
-        const uint64_t nwords = 1 + census_tail_chunks(P, c->sms);
+        // page_hits[P] | census tail: ticket + one word per chunk | list of flagged pages + count
+        const uint64_t nwords = census_tail_words(P, c->sms);
+        const uint64_t hb = (P * 4 + 255) & ~255ull, tb = (nwords * 8 + 255) & ~255ull;
         void *scr = nullptr;
-        if ((s = scratch(c, ((P * 4 + 255) & ~255ull) + nwords * 8, st, &scr)) != KC_OK) return s;
+        if ((s = scratch(c, hb + tb + (P + 1) * 4, st, &scr)) != KC_OK) return s;
         page_hits = static_cast<uint32_t *>(scr);
-        tail = reinterpret_cast<unsigned long long *>(static_cast<char *>(scr) + ((P * 4 + 255) & ~255ull));
+        tail = reinterpret_cast<unsigned long long *>(static_cast<char *>(scr) + hb);
+        list = reinterpret_cast<uint32_t *>(static_cast<char *>(scr) + hb + tb);
         aux.zero_words = tail;
         aux.nzero = nwords;
         aux.counts = d_counts;
@@ -642,7 +645,8 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
                  "digest launch");
     }
     if (census)
-        KC_CHECK(c, launch_census_tail(pg, t->ca, page_hits, tail, d_hits, cap, d_counts, status_word(c), c->sms, st),
+        KC_CHECK(c, launch_census_tail(pg, t->ca, page_hits, tail, list, d_hits, cap, d_counts, status_word(c), c->sms,
+                                       st),
                  "census tail");
     touch(c, t, st);
     return lost_status(c, t);

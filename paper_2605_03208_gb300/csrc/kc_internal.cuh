@@ -94,12 +94,13 @@ struct DigestAux {
 cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash, uint8_t *zero,
                           uint32_t *page_hits, uint32_t *task_ctr, uint32_t *status, const DigestShape &shape,
                           const DigestAux &aux, cudaStream_t st);
-// Census of the fused scan after the digest kernel (one launch).  tail:
-// 1 + census_tail_chunks(P, sms) words zeroed by the digest kernel.
-uint64_t census_tail_chunks(uint64_t npages, int sms);
+// Census of the fused scan after the digest kernel.  tail:
+// census_tail_words(P, sms) words zeroed by the digest kernel; list: P + 1
+// u32 of scratch.
+uint64_t census_tail_words(uint64_t npages, int sms);
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
-                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, int sms,
-                               cudaStream_t st);
+                               uint32_t *list, kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status,
+                               int sms, cudaStream_t st);
 cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
                                 uint64_t *counts, int sms, cudaStream_t st);
 cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca,
