@@ -578,26 +578,31 @@ __global__ void dd_table_kernel(Pages pg, const uint8_t *__restrict__ zero, cons
 // ---- small snapshots (P <= DD_SMALL pages) -------------------------------------
 //
 // The candidates for a page's class are the pages whose hashes share their
-// low 32 bits (as in the sort of the large path).  One CTA inserts every
-// data page into an open-addressing table in shared memory keyed by those
-// bits (32-bit atomics), keeping the smallest page id of each key (the
-// group's representative), so no sort is needed.  Pages whose full hashes
-// differ fail the byte comparison like any collision.  A page that is not its
-// group's representative is listed for a byte comparison with it
-// (dd_verify_rep_kernel).  With nothing to verify -- no two data pages share
-// a hash -- the same CTA assigns blob ids and writes the page table; else
-// dd_small_finish_kernel does so after the verification: a group whose
-// members all equal the representative is one class, and a group with a
-// failed comparison (a hash collision, or equal hashes of pages of different
-// lengths) is split by direct comparison exactly as the class definition
-// reads (members in increasing page id, each compared with the classes found
-// so far).
+// low 32 bits (as in the sort of the large path).  The key space is split
+// over DD_PARTS CTAs by its top bits; each CTA inserts its share of the data
+// pages into an open-addressing table in shared memory keyed by those 32 bits
+// (32-bit atomics), keeping the smallest page id of each key (the group's
+// representative), so no sort is needed and the atomics of one SM handle a
+// DD_PARTS-th of the pages.  Pages whose full hashes differ fail the byte
+// comparison like any collision.  A page that is not its group's
+// representative is listed for a byte comparison with it
+// (dd_verify_rep_kernel); the list's order does not matter.  Each CTA also
+// writes a slice of the page table as if every data page were canonical
+// (blob ids = data pages numbered in page order, which every CTA can count
+// from the zero flags alone); that is the table when no two data pages share
+// a key.  Otherwise dd_small_finish_kernel rewrites it after the
+// verification: a group whose members all equal the representative is one
+// class, and a group with a failed comparison (a hash collision, or equal
+// hashes of pages of different lengths) is split by direct comparison exactly
+// as the class definition reads (members in increasing page id, each
+// compared with the classes found so far).
 
 constexpr int DD_SMALL = 8192;                              // pages
 constexpr int DD_SMALL_THREADS = 1024;
 constexpr int DD_SMALL_PER = DD_SMALL / DD_SMALL_THREADS;   // pages per thread, blocked
 constexpr int DD_TABLE = 2 * DD_SMALL;                      // hash-table slots
 constexpr uint32_t DD_EMPTY = 0xffffffffu;
+constexpr int DD_PARTS = 8;                                 // CTAs of the grouping kernel
 constexpr size_t DD_SMALL_SMEM = (size_t)DD_TABLE * 4 + (size_t)DD_TABLE * 4 + (size_t)DD_SMALL * 2;
 constexpr size_t DD_FINISH_SMEM = (size_t)DD_SMALL * 4 * 4 + (size_t)DD_SMALL * 2 + (size_t)DD_SMALL;
 
@@ -687,6 +692,12 @@ __device__ __forceinline__ uint32_t dd_slot(uint32_t k) {
     return (k ^ (k >> 14) ^ (k >> 28)) & (DD_TABLE - 1);
 }
 
+// The CTA that owns a 32-bit key (its top bits).
+__device__ __forceinline__ uint32_t dd_part(uint32_t k, uint32_t nparts) {
+    return (uint32_t)(((uint64_t)k * nparts) >> 32);
+}
+
+// misc[2] (the count of listed pages) must be 0 at launch.
 __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     Pages pg, const uint64_t *__restrict__ hash, const uint8_t *__restrict__ zero, uint64_t *__restrict__ misc,
     uint32_t *__restrict__ rep_out, uint32_t *__restrict__ dups, uint32_t *__restrict__ neq,
@@ -694,23 +705,22 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     extern __shared__ __align__(16) uint8_t sm[];
     uint32_t *tkey = reinterpret_cast<uint32_t *>(sm);                       // [DD_TABLE] low 32 hash bits
     uint32_t *tval = tkey + DD_TABLE;                                        // [DD_TABLE]
-    uint16_t *mark = reinterpret_cast<uint16_t *>(tval + DD_TABLE);          // [DD_SMALL]
+    uint16_t *regs = reinterpret_cast<uint16_t *>(tval + DD_TABLE);          // [DD_SMALL]
     __shared__ uint32_t ws[33];
     __shared__ uint32_t empty_min;   // smallest data page whose key equals the empty-slot marker
+    __shared__ uint32_t dup_base;
     const int tid = threadIdx.x;
     const uint32_t P = (uint32_t)pg.npages;
+    const uint32_t part = blockIdx.x, nparts = gridDim.x;
 
     for (int i = tid; i < DD_TABLE; i += blockDim.x) {
         tkey[i] = DD_EMPTY;
         tval[i] = 0xffffffffu;
     }
     if (tid == 0) empty_min = 0xffffffffu;
-    uint32_t reg[DD_SMALL_PER];
-    small_regions(pg, mark, ws, reg);   // (its barriers also order the initialisation above)
 
-    // insert: key = low 32 hash bits, value = smallest page id with it
+    // the thread's DD_SMALL_PER consecutive pages: keys, zero flags, regions
     uint32_t h[DD_SMALL_PER];
-    uint32_t isdata = 0;
     uint8_t zf[DD_SMALL_PER];
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {   // all loads first: one memory round trip
@@ -718,20 +728,38 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
         zf[j] = p < P ? __ldg(zero + p) : (uint8_t)KC_PAGE_ZERO;
         h[j] = p < P ? (uint32_t)__ldg(hash + p) : 0u;
     }
+    uint32_t reg[DD_SMALL_PER];
+    {
+        const uint32_t p0 = tid * DD_SMALL_PER;
+        int r = p0 < P ? region_of(pg.regions, pg.nregions, p0) : 0;
 #pragma unroll
-    for (int j = 0; j < DD_SMALL_PER; ++j) isdata |= (uint32_t)(zf[j] == KC_PAGE_DATA) << j;
-    // first insertion attempt of every page at once; a taken slot (another
-    // key) continues along the probe chain
+        for (int j = 0; j < DD_SMALL_PER; ++j) {
+            const uint64_t p = p0 + j;
+            while (p < P && r + 1 < pg.nregions && __ldg(&pg.regions[r + 1].first) <= p) ++r;
+            reg[j] = (uint32_t)r;
+        }
+    }
+    uint32_t isdata = 0, mine = 0;
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const bool d = zf[j] == KC_PAGE_DATA;
+        isdata |= (uint32_t)d << j;
+        mine |= (uint32_t)(d && dd_part(h[j], nparts) == part) << j;
+    }
+    __syncthreads();   // table initialised
+
+    // insert this CTA's keys: value = smallest page id with the key.  The
+    // first insertion attempt of every page is issued at once; a taken slot
+    // (another key) continues along the probe chain
     uint32_t prev[DD_SMALL_PER];
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
         prev[j] = DD_EMPTY;
-        if (((isdata >> j) & 1) && h[j] != DD_EMPTY)
-            prev[j] = atomicCAS(&tkey[dd_slot(h[j])], DD_EMPTY, h[j]);
+        if (((mine >> j) & 1) && h[j] != DD_EMPTY) prev[j] = atomicCAS(&tkey[dd_slot(h[j])], DD_EMPTY, h[j]);
     }
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
-        if (!((isdata >> j) & 1)) continue;
+        if (!((mine >> j) & 1)) continue;
         const uint32_t p = tid * DD_SMALL_PER + j;
         if (h[j] == DD_EMPTY) {
             atomicMin(&empty_min, p);
@@ -749,20 +777,20 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
         atomicMin(&tval[s], p);
     }
     __syncthreads();
-    // look up each data page's representative: the first probe of every
-    // page is issued at once, the rest of a probe chain only on a miss
+    // look up each of this CTA's pages' representative: the first probe of
+    // every page is issued at once, the rest of a probe chain only on a miss
     uint32_t rep[DD_SMALL_PER], slot[DD_SMALL_PER], k0[DD_SMALL_PER];
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
         slot[j] = dd_slot(h[j]);
-        k0[j] = tkey[slot[j]];
+        k0[j] = ((mine >> j) & 1) ? tkey[slot[j]] : 0u;
     }
     uint32_t nd = 0;
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
         const uint32_t p = tid * DD_SMALL_PER + j;
         rep[j] = p;
-        if (!((isdata >> j) & 1)) continue;
+        if (!((mine >> j) & 1)) continue;
         if (h[j] == DD_EMPTY) {
             rep[j] = empty_min;
         } else if (k0[j] == h[j]) {
@@ -777,36 +805,63 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
         }
         nd += rep[j] != p;
     }
-    uint32_t ndup = 0;
-    uint32_t o = block_excl_sum(nd, ws, &ndup);
-    if (ndup == 0) {
-        // no two data pages share a hash: every data page is canonical (the
-        // hash table's memory is reused: it is no longer needed)
-        uint32_t *bid = tval;
-        uint32_t *cano = tkey;
-        small_table(pg, zero, reg, [&](int j) { return (uint32_t)(tid * DD_SMALL_PER + j); }, bid, cano, mark, ws,
-                    table, blob_page, misc, n_blobs_out);
-        if (tid == 0) {
-            misc[0] = P;
-            misc[2] = 0;
-        }
-        return;
-    }
-    // pages to verify, in increasing page id, and every data page's representative
+    // pages to verify (appended at a CTA-wide offset) and each of this CTA's
+    // data pages' representative
+    uint32_t ndc = 0;
+    uint32_t o = block_excl_sum(nd, ws, &ndc);   // (its barriers end the table's use)
+    if (tid == 0)
+        dup_base = ndc ? (uint32_t)atomicAdd(reinterpret_cast<unsigned long long *>(&misc[2]), (unsigned long long)ndc)
+                       : 0u;
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
+        if (!((mine >> j) & 1)) continue;
         const uint32_t p = tid * DD_SMALL_PER + j;
-        if (p >= P) continue;
         rep_out[p] = rep[j];
-        if (rep[j] != p) {
-            dups[o] = p;
+    }
+
+    // the table as if every data page were canonical: blob id = data pages
+    // before it; this CTA writes the rows of its slice of pages
+    uint32_t nb = 0;
+    uint32_t r0 = block_excl_sum((uint32_t)__popc(isdata), ws, &nb);   // (its barriers publish dup_base)
+    o += dup_base;
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        if (((mine >> j) & 1) && rep[j] != tid * DD_SMALL_PER + j) {
+            dups[o] = tid * DD_SMALL_PER + j;
             neq[o] = 0;
             ++o;
         }
     }
-    if (tid == 0) {
+    const uint32_t span = (P + nparts - 1) / nparts;
+    const uint32_t lo = part * span < P ? part * span : P;
+    const uint32_t hi = lo + span < P ? lo + span : P;
+    uint32_t *bid = tkey;   // [DD_SMALL] blob id of each data page of the slice
+#pragma unroll
+    for (int j = 0; j < DD_SMALL_PER; ++j) {
+        const uint32_t p = tid * DD_SMALL_PER + j;
+        if (p >= lo && p < hi) {
+            regs[p] = (uint16_t)reg[j];
+            if ((isdata >> j) & 1) {
+                bid[p] = r0;
+                blob_page[r0] = p;
+            }
+        }
+        r0 += (isdata >> j) & 1;
+    }
+    __syncthreads();
+    for (uint32_t p = lo + tid; p < hi; p += blockDim.x) {
+        const uint8_t z = zero[p];
+        const uint32_t r = regs[p];
+        kc_page row;
+        row.va_offset = (p - __ldg(&pg.regions[r].first)) << pg.log2page;
+        row.alloc_id = r;
+        row.blob = z == KC_PAGE_ZERO ? KC_BLOB_ZERO : z == KC_PAGE_LOST ? KC_BLOB_LOST : bid[p];
+        table[p] = row;
+    }
+    if (part == 0 && tid == 0) {
         misc[0] = P;
-        misc[2] = ndup;
+        misc[1] = nb;
+        if (n_blobs_out) *n_blobs_out = nb;
     }
 }
 
@@ -981,11 +1036,12 @@ cudaError_t run_dedup(const Pages &pg, const uint64_t *hash, const uint8_t *zero
     const unsigned g = grid_for(P, 256, sms, 8);
     const uint32_t pieces = (pg.page + DD_PIECE - 1) / DD_PIECE;
     if (P <= (uint64_t)DD_SMALL) {
-        // small: grouping by a shared-memory hash table in one CTA, the wide
-        // verification of pages sharing a hash, and (only when there were
-        // such pages) the classes and table in a second CTA
-        dd_small_kernel<<<1, DD_SMALL_THREADS, DD_SMALL_SMEM, st>>>(pg, hash, zero, s.misc, s.canon, s.dups, s.neq,
-                                                                    table, s.blob_page, n_blobs);
+        // small: grouping by shared-memory hash tables (the keys split over
+        // DD_PARTS CTAs), the wide verification of pages sharing a key, and
+        // (only when there were such pages) the classes and table in one CTA
+        KC_TRY(cudaMemsetAsync(s.misc + 2, 0, 8, st));
+        dd_small_kernel<<<DD_PARTS, DD_SMALL_THREADS, DD_SMALL_SMEM, st>>>(pg, hash, zero, s.misc, s.canon, s.dups,
+                                                                           s.neq, table, s.blob_page, n_blobs);
         count_launches(1);
         KC_TRY(cudaGetLastError());
         dd_verify_rep_kernel<<<grid_for(P * pieces * 32, 256, sms, 8), 256, 0, st>>>(pg, s.dups, s.canon, s.misc,

@@ -152,8 +152,10 @@ def test_census_dense_pointers_and_truncation(ctx):
 
 # ---------------------------------------------------------------- dedup / restore
 
-def _dedup_vs_oracle(ctx, snap, dev, S, hash_bits=64, low_bits=None):
+def _dedup_vs_oracle(ctx, snap, dev, S, hash_bits=64, low_bits=None, xform=None):
     oh, oz, _ = _oracle_digest(snap, S)
+    if xform is not None:
+        oh = xform(oh)
     if hash_bits < 64:
         oh = oh & np.uint64((1 << hash_bits) - 1)
     if low_bits is not None:
@@ -193,6 +195,31 @@ def test_dedup_low_half_collisions(ctx, tiny, low_bits):
     order; the result must still be the byte-defined classes."""
     snap, dev = tiny
     _dedup_vs_oracle(ctx, snap, dev, 4096, low_bits=low_bits)
+
+
+def test_dedup_no_shared_keys(ctx):
+    """No copies: every data page is its own class, and the grouping kernel's
+    own table (data pages numbered in page order) is the result."""
+    snap, dev = G.device_snapshot(W.tiny_layout(3), W.tiny_fill, 3, p_copy=0.0)
+    t, _, nb = _dedup_vs_oracle(ctx, snap, dev, 4096)
+    data = t["blob"][t["blob"] < kc.BLOB_LOST]
+    assert nb == len(data) and np.array_equal(data, np.arange(nb))
+
+
+@pytest.mark.parametrize("every", [1, 3])
+def test_dedup_empty_marker_key(ctx, tiny, every):
+    """Hashes whose low 32 bits equal the table's empty-slot marker (all ones)
+    are grouped outside the table; mixed with ordinary keys (every 3rd page)
+    and alone (every page).  All such pages form one group that fails its
+    byte comparison, so the exact slow path splits it (64 KiB pages keep that
+    quadratic split small)."""
+    snap, dev = tiny
+
+    def xform(oh):
+        oh = oh.copy()
+        oh[::every] |= np.uint64(0xFFFFFFFF)
+        return oh
+    _dedup_vs_oracle(ctx, snap, dev, 65536, xform=xform)
 
 
 def test_dedup_tiled_sort_path(ctx):
