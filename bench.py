@@ -229,15 +229,19 @@ class KcStep:
 # DRAM traffic of one digest_kernel<census> launch on this workload, from the
 # ncu capture summarised in profiles/digest_kernel_llama400.md, valid only for
 # the kernel sources it was taken on (sha1 of each file, first 8 hex digits).
-DIGEST_TRAFFIC = {"bytes": 402_745_088 + 3_981_056,
+DIGEST_TRAFFIC = {"bytes": 402_742_016 + 3_258_624,
+                  "shape": {"warps": 2, "stages": 2, "chunk": 1024, "ctas": 396, "lanes": 1},
                   "sources": {"k_digest.cu": "29459998", "digest_task.cuh": "411ed35a",
                               "kc_device.cuh": "d43b1599"}}
 
 
-def digest_traffic():
+def digest_traffic(shape):
     """DRAM bytes per digest launch measured by ncu, or None once any of the
-    kernel's sources differs from the ones the capture was taken on."""
+    kernel's sources, or the launch shape, differs from the ones the capture
+    was taken on."""
     import hashlib
+    if shape != DIGEST_TRAFFIC["shape"]:
+        return None
     for f, want in DIGEST_TRAFFIC["sources"].items():
         path = os.path.join(ROOT, "paper_2605_03208_gb300", "csrc", f)
         try:
@@ -513,7 +517,8 @@ def run_kc(args):
         "roofline": {"bound": "hbm", "kernel": "digest_kernel<census> (kc_scan)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": digest_traffic(), "algorithmic_bytes": scan_bytes,
+                     "traffic": digest_traffic(ctx.digest_shape(step.S, step.P)),
+                     "shape": ctx.digest_shape(step.S, step.P), "algorithmic_bytes": scan_bytes,
                      "kernel_ms": op_ms["digest_kernel"]},
         "ops": {op: {"ms": op_ms[op], "GB/s": ab[op] / (op_ms[op] / 1000) / 1e9,
                      "frac": ab[op] / (op_ms[op] / 1000) / 1e9 / peak,
