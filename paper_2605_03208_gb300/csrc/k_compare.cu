@@ -121,7 +121,7 @@ cudaError_t launch_compare(const CmpPair *pairs, int npairs, uint64_t ntiles, do
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || ntiles == 0) return e;
     uint64_t blocks = ntiles;
-    const uint64_t maxb = (uint64_t)sms * 8;
+    const uint64_t maxb = (uint64_t)sms * 6;   // 2 waves of 3 resident CTAs per SM: measured best of 3..8
     if (blocks > maxb) blocks = maxb;
     cmp_kernel<<<(unsigned)blocks, CMP_THREADS, 0, st>>>(pairs, npairs, ntiles, atol, rtol, out);
     count_launches(1);
