@@ -7,6 +7,8 @@ Sizes: the tiny mixed snapshot (16 regions, ~16 MiB, ragged tails) spans
 hundreds of 8-page digest tasks and compare tiles; page sizes 4 KiB..2 MiB
 and forced kernel shapes cover one-stage to deep rings.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -78,6 +80,33 @@ def test_digest_edge_lengths(ctx):
         oh, oz, opf = _oracle_digest(snap, S)
         assert st == kc.OK
         assert np.array_equal(h, oh) and np.array_equal(z, oz) and np.array_equal(pf, opf)
+
+
+def _golden_xxh64():
+    path = os.path.join(os.path.dirname(__file__), "golden", "xxh64_edges.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, seed, h = line.split()
+                rows.append((int(n), int(seed, 16), int(h, 16)))
+    return rows
+
+
+def test_digest_golden_xxh64_edges(ctx):
+    """kc_digest against the stored XXH64 values (seed 0) of every tail path:
+    one region per length, a page size above every length, so each region is
+    one page whose hash is XXH64 of the whole region."""
+    rows = [(n, h) for n, seed, h in _golden_xxh64() if seed == 0 and n > 0]
+    regions = [((np.arange(n, dtype=np.int64) * 131 + 7) % 251).astype(np.uint8) for n, _ in rows]
+    dev = [torch.from_numpy(r).cuda() for r in regions]
+    sizes = [n for n, _ in rows]
+    snap = W.Snapshot("golden-edges", 131072, sizes, [t.data_ptr() for t in dev], regions, [kc.RAW] * len(sizes))
+    st, h, z, pf = G.run_digest(ctx, snap, dev, 131072)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    assert np.array_equal(pf, np.arange(len(rows) + 1))
+    assert [int(x) for x in h.view(np.uint64)] == [hv for _, hv in rows]
+    assert not z.any()
 
 
 # ---------------------------------------------------------------- census

@@ -6,6 +6,8 @@
 - Page splitting against the closed form ceil(bytes / S).
 - Zero flags against the pages the generator planted as zero.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -83,3 +85,30 @@ def test_digest_partial_pages_are_not_padded():
     assert list(z) == [1, 0]
     # an all-zero page is still hashed: XXH64 of that many zero bytes
     assert h[0] == oracle.xxh64(bytes(4096))
+
+
+def _golden_rows():
+    path = os.path.join(os.path.dirname(__file__), "golden", "xxh64_edges.txt")
+    with open(path) as f:
+        return [tuple(int(x, 0) for x in line.split()) for line in f if line.strip() and not line.startswith("#")]
+
+
+def _pattern(n):
+    return bytes((i * 131 + 7) % 251 for i in range(n))
+
+
+def test_golden_xxh64_edges_reproduced_by_oracle():
+    """The stored values are the oracle's (regression guard for the file)."""
+    rows = _golden_rows()
+    assert len(rows) == 4 * 87
+    for n, seed, h in rows:
+        assert oracle.xxh64(_pattern(n), seed) == h
+
+
+@needs_xxh
+def test_golden_xxh64_edges_match_libxxhash():
+    """The stored values agree with the xxHash project's implementation, so the
+    GPU tests that compare kc_digest with the file are pinned where libxxhash
+    is not installed."""
+    for n, seed, h in _golden_rows():
+        assert xxh_ref(_pattern(n), seed) == h
