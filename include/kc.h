@@ -237,8 +237,9 @@ KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, 
                                   kc_hit *d_hits, uint64_t cap, uint64_t *d_counts, void *stream);
 
 /* kc_scan: kc_digest and kc_census fused into one read of the snapshot
- * (the census is counted while pages are hashed, then only pages that hold
- * hits are read a second time to write them in order).  Outputs and errors
+ * (while pages are hashed, a conservative test on the high 32 bits of every
+ * word flags the pages that may hold hits; only those are read a second
+ * time, classified and written in order).  Outputs and errors
  * are exactly those of the two calls. */
 KC_API kc_status kc_scan(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page_bytes,
                   uint64_t *d_hash, uint8_t *d_zero, uint64_t *d_page_first,
@@ -247,8 +248,9 @@ KC_API kc_status kc_scan(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page
 
 /* ---- dedup ----------------------------------------------------------------
  * Input: the digest of the same regions at the same page size (d_hash,
- * d_zero).  Non-zero pages are grouped by a device radix sort of their
- * hashes and byte-verified; two pages are duplicates iff they have the same
+ * d_zero).  Non-zero pages are grouped by their hashes (a device radix sort;
+ * up to 8192 pages, shared-memory hash tables) and byte-verified; the
+ * grouping never decides a result: two pages are duplicates iff they have the same
  * length and the same bytes.  canonical(p) = the smallest page id of p's
  * class; blobs are numbered 0, 1, ... in increasing canonical page id.
  * d_table[p] = {j * S, i, blob(canonical(p))}, KC_BLOB_ZERO for zero pages,
