@@ -328,6 +328,24 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest x over the ranks of the process group (the slowest
+    replica sets the job's time); x itself when there is one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbps(world: int, bytes_per_replica_step: float, ms_per_step: float) -> float:
+    """Whole-job throughput: every replica processes its own snapshot of the
+    same size in each step, and the step takes the slowest replica's time."""
+    return world * bytes_per_replica_step / (ms_per_step / 1000) / 1e9
+
+
 # ----------------------------------------------------------------------------- GPU leg
 
 def run_kc(args):
@@ -405,11 +423,7 @@ def run_kc(args):
     barrier()
     t_wall1 = time.time()
     launches = launches_per_step * args.steps
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world, device)
     ms = ms_total / args.steps
     time.sleep(0.3)
     sampler.stop()
@@ -493,14 +507,10 @@ def run_kc(args):
         stream.wait_stream(L["s"])
     f1.record(stream)
     barrier()
-    e2e_ms = f0.elapsed_time(f1) / k_e2e
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / k_e2e, world, device)
 
     peak, peak_kind = peaks()
-    value = world * step_bytes / (ms / 1000) / 1e9
+    value = whole_job_gbps(world, step_bytes, ms)
     scan_bytes = ab["scan"]
     achieved = scan_bytes / (op_ms["digest_kernel"] / 1000) / 1e9
     line = {
@@ -527,7 +537,7 @@ def run_kc(args):
                       "kernels); the roofline kernel is timed by events the library records around it "
                       "alone; the timed region replays the step as a CUDA graph (no events inside)",
         "launches_per_step": launches_per_step,
-        "e2e": {"value": world * step_bytes / (e2e_ms / 1000) / 1e9, "unit": "GB/s",
+        "e2e": {"value": whole_job_gbps(world, step_bytes, e2e_ms), "unit": "GB/s",
                 "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ingest": "kc_restore with the identity page table reads the page-slotted snapshot image "
                           "from pinned host memory; compare inputs copied in; outputs read back every step; "
