@@ -705,7 +705,6 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     extern __shared__ __align__(16) uint8_t sm[];
     uint32_t *tkey = reinterpret_cast<uint32_t *>(sm);                       // [DD_TABLE] low 32 hash bits
     uint32_t *tval = tkey + DD_TABLE;                                        // [DD_TABLE]
-    uint16_t *regs = reinterpret_cast<uint16_t *>(tval + DD_TABLE);          // [DD_SMALL]
     __shared__ uint32_t ws[33];
     __shared__ uint32_t empty_min;   // smallest data page whose key equals the empty-slot marker
     __shared__ uint32_t dup_base;
@@ -719,7 +718,7 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     }
     if (tid == 0) empty_min = 0xffffffffu;
 
-    // the thread's DD_SMALL_PER consecutive pages: keys, zero flags, regions
+    // the thread's DD_SMALL_PER consecutive pages: keys and zero flags
     uint32_t h[DD_SMALL_PER];
     uint8_t zf[DD_SMALL_PER];
 #pragma unroll
@@ -727,17 +726,6 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
         const uint32_t p = tid * DD_SMALL_PER + j;
         zf[j] = p < P ? __ldg(zero + p) : (uint8_t)KC_PAGE_ZERO;
         h[j] = p < P ? (uint32_t)__ldg(hash + p) : 0u;
-    }
-    uint32_t reg[DD_SMALL_PER];
-    {
-        const uint32_t p0 = tid * DD_SMALL_PER;
-        int r = p0 < P ? region_of(pg.regions, pg.nregions, p0) : 0;
-#pragma unroll
-        for (int j = 0; j < DD_SMALL_PER; ++j) {
-            const uint64_t p = p0 + j;
-            while (p < P && r + 1 < pg.nregions && __ldg(&pg.regions[r + 1].first) <= p) ++r;
-            reg[j] = (uint32_t)r;
-        }
     }
     uint32_t isdata = 0, mine = 0;
 #pragma unroll
@@ -820,9 +808,14 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
     }
 
     // the table as if every data page were canonical: blob id = data pages
-    // before it; this CTA writes the rows of its slice of pages
+    // before it; this CTA writes the rows of its slice of pages.  The
+    // regions' first pages go to the table's memory (every region holds a
+    // page, so there are at most P <= DD_SMALL of them) for the page ->
+    // region search.
+    uint64_t *sfirst = reinterpret_cast<uint64_t *>(tval);
+    for (int a = tid; a < pg.nregions; a += blockDim.x) sfirst[a] = __ldg(&pg.regions[a].first);
     uint32_t nb = 0;
-    uint32_t r0 = block_excl_sum((uint32_t)__popc(isdata), ws, &nb);   // (its barriers publish dup_base)
+    uint32_t r0 = block_excl_sum((uint32_t)__popc(isdata), ws, &nb);   // (its barriers publish dup_base, sfirst)
     o += dup_base;
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
@@ -839,22 +832,24 @@ __global__ void __launch_bounds__(DD_SMALL_THREADS) dd_small_kernel(
 #pragma unroll
     for (int j = 0; j < DD_SMALL_PER; ++j) {
         const uint32_t p = tid * DD_SMALL_PER + j;
-        if (p >= lo && p < hi) {
-            regs[p] = (uint16_t)reg[j];
-            if ((isdata >> j) & 1) {
-                bid[p] = r0;
-                blob_page[r0] = p;
-            }
+        if (p >= lo && p < hi && ((isdata >> j) & 1)) {
+            bid[p] = r0;
+            blob_page[r0] = p;
         }
         r0 += (isdata >> j) & 1;
     }
     __syncthreads();
     for (uint32_t p = lo + tid; p < hi; p += blockDim.x) {
         const uint8_t z = zero[p];
-        const uint32_t r = regs[p];
+        int rl = 0, rh = pg.nregions - 1;   // last region whose first page <= p
+        while (rl < rh) {
+            const int mid = (rl + rh + 1) >> 1;
+            if (sfirst[mid] <= p) rl = mid;
+            else rh = mid - 1;
+        }
         kc_page row;
-        row.va_offset = (p - __ldg(&pg.regions[r].first)) << pg.log2page;
-        row.alloc_id = r;
+        row.va_offset = (p - sfirst[rl]) << pg.log2page;
+        row.alloc_id = (uint32_t)rl;
         row.blob = z == KC_PAGE_ZERO ? KC_BLOB_ZERO : z == KC_PAGE_LOST ? KC_BLOB_LOST : bid[p];
         table[p] = row;
     }
