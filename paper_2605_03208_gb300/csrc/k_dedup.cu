@@ -20,8 +20,9 @@
 //   5. blob ids = exclusive scan of "page is canonical" in page order; the
 //      page table is written VA-faithfully (region index, offset);
 //   6. pack copies every canonical page into its arena slot, zero-filled.
-// Snapshots of at most DD_SMALL pages replace steps 1-5 by a hash table in
-// one CTA's shared memory (no sort; see "small snapshots" below).
+// Snapshots of at most DD_SMALL pages replace steps 1-5 by hash tables in
+// shared memory, the keys split over DD_PARTS CTAs (no sort; see "small
+// snapshots" below).
 #include <cuda_runtime.h>
 
 #include "kc_device.cuh"
