@@ -162,29 +162,6 @@ __device__ __forceinline__ void warp_rank(const uint64_t (&key)[ITEMS], int shif
     }
 }
 
-// Exclusive scan of 256 digit totals by one warp (8 digits per lane).
-__device__ __forceinline__ void digit_bases(const uint32_t *dsum, uint32_t *dbase) {
-    const int lane = threadIdx.x & 31;
-    uint32_t v[8], loc = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        v[j] = dsum[lane * 8 + j];
-        loc += v[j];
-    }
-    uint32_t inc = loc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    uint32_t run = inc - loc;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        dbase[lane * 8 + j] = run;
-        run += v[j];
-    }
-}
-
 // Block-wide exclusive sum of one u32 per thread; *total gets the sum.
 // `ws` is 32 words of shared scratch.  Every thread must call it.
 __device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t *ws, uint32_t *total) {

@@ -1,5 +1,5 @@
-// kc_device.cuh -- device helpers: inline PTX for mbarriers and bulk
-// (TMA, non-tensor) copies, bounded waits, warp utilities, XXH64 pieces.
+// kc_device.cuh -- device helpers: warp utilities, asynchronous copies into
+// shared memory, XXH64 pieces, census classification.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,12 +8,6 @@
 #include "kc_internal.cuh"
 
 namespace kc {
-
-// Polls of an mbarrier before a wait is declared timed out: the first
-// SPIN_FAST polls spin, the rest back off with nanosleep, bounding a wait to
-// roughly a second.
-constexpr uint32_t SPIN_FAST = 256;
-constexpr uint32_t SPIN_LIMIT = 1u << 24;
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
@@ -25,66 +19,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// ---- mbarrier ---------------------------------------------------------------
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-// Make mbarrier initialisation visible to the async proxy (bulk copies).
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t tx) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-        "r"(tx)
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for phase `parity` of `bar` to complete, at most SPIN_LIMIT polls.
-// Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < SPIN_LIMIT; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i >= SPIN_FAST) __nanosleep(64);
-    }
-    return false;
-}
-
-// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
-// global memory into this CTA's shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes,
-                                         uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst_smem)),
-        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
 }
 
 // Per-thread asynchronous 16-byte copy global -> shared (both 16-byte
@@ -196,31 +130,6 @@ __device__ __forceinline__ uint64_t rotl(uint64_t x, int r) { return (x << r) | 
 // Accumulator step for one 8-byte lane of a stripe.
 __device__ __forceinline__ uint64_t xx_round(uint64_t acc, uint64_t lane) {
     return rotl(acc + lane * XXP2, 31) * XXP1;
-}
-
-// The same step with the lane product m = lane * PRIME2 already computed, in
-// 32-bit PTX: only the add, the rotate and the multiply by PRIME1 depend on
-// the previous accumulator, so the lane products of later stripes can be
-// computed while this chain runs.
-__device__ __forceinline__ uint64_t xx_step(uint64_t acc, uint64_t m) {
-    uint32_t olo, ohi;
-    asm("{\n\t.reg .u32 tl, th, rl, rh, h1, h2;\n\t"
-        "add.cc.u32 tl, %2, %4;\n\t"
-        "addc.u32 th, %3, %5;\n\t"
-        "shf.l.wrap.b32 rh, tl, th, 31;\n\t"
-        "shf.l.wrap.b32 rl, th, tl, 31;\n\t"
-        "mul.lo.u32 %0, rl, 0x85EBCA87;\n\t"
-        "mul.hi.u32 h1, rl, 0x85EBCA87;\n\t"
-        "mad.lo.u32 h2, rl, 0x9E3779B1, h1;\n\t"
-        "mad.lo.u32 %1, rh, 0x85EBCA87, h2;\n\t}"
-        : "=r"(olo), "=r"(ohi)
-        : "r"((uint32_t)acc), "r"((uint32_t)(acc >> 32)), "r"((uint32_t)m), "r"((uint32_t)(m >> 32)));
-    return ((uint64_t)ohi << 32) | olo;
-}
-
-// Seed-0 start value of accumulator k (0..3).
-__device__ __forceinline__ uint64_t xx_init(int k) {
-    return k == 0 ? XXP1 + XXP2 : k == 1 ? XXP2 : k == 2 ? 0ULL : 0ULL - XXP1;
 }
 
 // ---- the lane chain in "pre-rotate" form ---------------------------------------
