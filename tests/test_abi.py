@@ -82,3 +82,36 @@ def test_poll_flags_host_helper():
     assert lib.kc_poll_flags(f.ctypes.data, 5, idx) == 3 and list(idx[:3]) == [1, 3, 4]
     assert lib.kc_poll_flags(f.ctypes.data, 0, idx) == 0
     assert lib.kc_poll_flags(None, 5, idx) == -1 and lib.kc_poll_flags(f.ctypes.data, -1, idx) == -1
+
+
+def test_plain_c_client_builds_links_and_gets_errors_not_crashes(tmp_path):
+    """A C program that includes only include/kc.h and links libkc.so: the
+    host-only calls work, a context on a device that does not exist is
+    refused with an error (and no handle), and a call without a context is
+    refused before any device work."""
+    path = build.build()
+    src = tmp_path / "client.c"
+    src.write_text('''#include <stdio.h>
+#include <string.h>
+#include "kc.h"
+int main(void) {
+    kc_buf b[2] = {{0x1000, 4096 * 3 + 1, KC_RAW, 0}, {0x100000, 5, KC_RAW, 0}};
+    if (kc_version() != 1) return 1;
+    if (strcmp(kc_status_name(KC_ETRUNC), "KC_ETRUNC") != 0) return 2;
+    if (kc_page_count(b, 2, 4096) != 5) return 3;
+    kc_ctx *c = NULL;
+    kc_status s = kc_create(&c, 9999);
+    if (s == KC_OK || c != NULL) return 4;
+    if (kc_digest(NULL, b, 2, 4096, NULL, NULL, NULL, NULL) != KC_EINVAL) return 5;
+    if (kc_compare(NULL, b, b, 1, 0.0, 0.0, NULL, NULL) != KC_EINVAL) return 6;
+    printf("ok %s\\n", kc_status_name(s));
+    return 0;
+}
+''')
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(path)
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-l:" + os.path.basename(path), "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.startswith("ok KC_E")
