@@ -7,6 +7,7 @@ take.  There is no CPU fallback: if the library is missing, loading fails.
 from __future__ import annotations
 
 import ctypes
+import operator
 import os
 
 import numpy as np
@@ -149,11 +150,13 @@ def bufs(items) -> ctypes.Array:
 
 
 def _ptr(x) -> int:
+    """Address of a tensor (data_ptr), or an integer address (Python or numpy
+    integer) as given; None is 0."""
     if x is None:
         return 0
-    if isinstance(x, int):
-        return x
-    return x.data_ptr()
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return operator.index(x)
 
 
 def _stream(s):
