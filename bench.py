@@ -38,6 +38,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "GB/s & % HBM peak for digest+dedup+census+compare; batched vs plain; p99 ms"
+NOMINAL_HBM_GBPS = 7900.0   # GB300 HBM3e nominal; fractions are also given against the measured copy peak
 
 
 def parse():
@@ -526,9 +527,11 @@ def run_kc(args):
                    "step": "scan(digest+census) + dedup(+pack) + restore, and compare on a second "
                            "stream overlapped with them; timed as CUDA graph replays of the step"},
         "hbm_frac": value / world / peak,
+        "hbm_frac_of_nominal": value / world / NOMINAL_HBM_GBPS,
         "roofline": {"bound": "hbm", "kernel": "digest_kernel<census> (kc_scan)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBPS,
                      "traffic": digest_traffic(ctx.digest_shape(step.S, step.P)),
                      "shape": ctx.digest_shape(step.S, step.P), "algorithmic_bytes": scan_bytes,
                      "kernel_ms": op_ms["digest_kernel"]},
