@@ -49,29 +49,34 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _load(path: str):
+    """Open an oracle library at `path` and declare its functions."""
+    L = ctypes.CDLL(path)
+    u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+    L.kco_xxh64.restype = u64
+    L.kco_xxh64.argtypes = [vp, u64, u64]
+    L.kco_page_first.restype = u64
+    L.kco_page_first.argtypes = [i32, vp, u32, vp]
+    L.kco_digest.restype = None
+    L.kco_digest.argtypes = [i32, vp, vp, u32, vp, vp, vp]
+    L.kco_dedup.restype = i32
+    L.kco_dedup.argtypes = [i32, vp, vp, u32, vp, vp, vp, vp, vp, vp, vp]
+    L.kco_pack.restype = None
+    L.kco_pack.argtypes = [i32, vp, vp, u32, vp, vp, vp, vp, vp]
+    L.kco_restore.restype = None
+    L.kco_restore.argtypes = [i32, vp, vp, u32, u64, vp, vp, vp, vp]
+    L.kco_census.restype = i32
+    L.kco_census.argtypes = [i32, vp, vp, vp, vp, u64, u64, vp, u64, vp, vp]
+    L.kco_compare.restype = None
+    L.kco_compare.argtypes = [vp, vp, i32, u64, ctypes.c_double, ctypes.c_double, vp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
-            u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
-            L.kco_xxh64.restype = u64
-            L.kco_xxh64.argtypes = [vp, u64, u64]
-            L.kco_page_first.restype = u64
-            L.kco_page_first.argtypes = [i32, vp, u32, vp]
-            L.kco_digest.restype = None
-            L.kco_digest.argtypes = [i32, vp, vp, u32, vp, vp, vp]
-            L.kco_dedup.restype = i32
-            L.kco_dedup.argtypes = [i32, vp, vp, u32, vp, vp, vp, vp, vp, vp, vp]
-            L.kco_pack.restype = None
-            L.kco_pack.argtypes = [i32, vp, vp, u32, vp, vp, vp, vp, vp]
-            L.kco_restore.restype = None
-            L.kco_restore.argtypes = [i32, vp, vp, u32, u64, vp, vp, vp, vp]
-            L.kco_census.restype = i32
-            L.kco_census.argtypes = [i32, vp, vp, vp, vp, u64, u64, vp, u64, vp, vp]
-            L.kco_compare.restype = None
-            L.kco_compare.argtypes = [vp, vp, i32, u64, ctypes.c_double, ctypes.c_double, vp]
-            _lib = L
+            _lib = _load(build())
         return _lib
 
 

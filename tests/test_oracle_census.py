@@ -85,6 +85,18 @@ def test_census_half_open_ranges_and_window():
     assert (nin, nout) == (4, 3)
 
 
+def test_census_window_edges():
+    """The window is half-open too: win_lo itself is an outside hit, the
+    last word below win_hi is, win_hi and the word below win_lo are not."""
+    base = [0x100000]
+    lo, hi = 0x8000, 0x28000
+    vals = np.array([lo, lo - 8, hi - 8, hi, hi - 1, lo + 1], dtype=np.uint64)
+    r0 = vals.view(np.uint8).copy()
+    hits, nin, nout, rc = oracle.census([r0], base, lo, hi)
+    assert _as_tuples(hits) == [(0, 0, lo, -1), (0, 16, hi - 8, -1), (0, 32, hi - 1, -1), (0, 40, lo + 1, -1)]
+    assert (nin, nout, rc) == (0, 4, 0)
+
+
 def test_census_truncation_keeps_true_counts_and_overlap_rejected():
     snap = W.tiny_layout(1, n=6, total=1 * W.MiB)
     snap = W.tiny_fill(snap, W.fake_bases(snap.sizes, 1), 1, p_ptr=0.5)

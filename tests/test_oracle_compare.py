@@ -81,6 +81,22 @@ def test_tolerances_against_isclose(atol, rtol):
     check(rec, expected(got, want, W.DT_F32, atol, rtol))
 
 
+def test_tolerance_scales_with_want_not_got():
+    """rtol multiplies |want| (numpy.isclose's b): pairs whose verdict flips
+    when it multiplies |got| instead, in fp32, fp16 and int32."""
+    want = np.array([1.0, 1.0, 4.0, -2.0, 10.0, 0.5], dtype=np.float64)
+    got = np.array([1.5, 0.7, 2.0, -1.0, 6.5, 0.75], dtype=np.float64)
+    for dt, npdt in ((W.DT_F32, np.float32), (W.DT_F16, np.float16)):
+        g, w = got.astype(npdt), want.astype(npdt)
+        rec = oracle.compare(g, w, dt, 0.0, 0.4)
+        check(rec, expected(g, w, dt, 0.0, 0.4))
+        assert rec["mismatches"] == 4 and rec["first"] == 0      # elements 0, 2, 3, 5
+    gi, wi = np.array([15, 7, 40, -10], dtype=np.int32), np.array([10, 10, 40, -20], dtype=np.int32)
+    rec = oracle.compare(gi, wi, W.DT_I32, 0.0, 0.4)
+    check(rec, expected(gi, wi, W.DT_I32, 0.0, 0.4))
+    assert rec["mismatches"] == 2 and rec["first"] == 0          # elements 0, 3
+
+
 def test_identical_buffers_compare_clean():
     rng = np.random.default_rng(0)
     for dt, arr in [(W.DT_F32, rng.standard_normal(5000, dtype=np.float32)),

@@ -112,3 +112,22 @@ def test_golden_xxh64_edges_match_libxxhash():
     is not installed."""
     for n, seed, h in _golden_rows():
         assert xxh_ref(_pattern(n), seed) == h
+
+
+def test_zero_flag_is_every_byte_of_the_page():
+    """The zero flag by construction: a page with exactly one non-zero byte
+    (first, second, middle or last byte of a full page; last byte of a
+    partial page) is not zero, an all-zero partial page is."""
+    S = 4096
+    positions = [0, 1, S // 2, S - 1]
+    regions = []
+    for pos in positions:
+        r = np.zeros(S, dtype=np.uint8)
+        r[pos] = 1
+        regions.append(r)
+    tail = np.zeros(S + 100, dtype=np.uint8)
+    tail[S + 99] = 0x80
+    regions.append(tail)                       # pages: zero, then partial with its last byte set
+    regions.append(np.zeros(S + 7, dtype=np.uint8))   # pages: zero, partial zero
+    _, z, _ = oracle.digest(regions, S)
+    assert z.tolist() == [0, 0, 0, 0, 1, 0, 1, 1]
