@@ -87,12 +87,15 @@ MUTANTS = [
      "if (canon[p] == p) blob_of[p] = next++;", _dedup_pins),
     ("restore leaves zero pages unwritten", "if (tbl_blob[p] == KCO_BLOB_ZERO) memset(img[a] + off, 0, (size_t)len);",
      "if (tbl_blob[p] == KCO_BLOB_ZERO) (void)0;", _dedup_pins),
+    ("equal hashes taken as equal pages", "if (pages_equal(n, img, bytes, pf, S, p, reps[r])) break;",
+     "if (1) break;", _dedup_pins),
     # census
     ("range end inclusive", "if (lo > 0 && v < rg[lo - 1].end)", "if (lo > 0 && v <= rg[lo - 1].end)", _census_pins),
     ("window start exclusive", "else if (win_lo <= v && v < win_hi)", "else if (win_lo < v && v < win_hi)",
      _census_pins),
     ("last word of a region skipped", "for (uint64_t o = 0; o + 8 <= lim; o += 8)",
      "for (uint64_t o = 0; o + 16 <= lim; o += 8)", _census_pins),
+    ("outside hits counted as inside", "{ target = -1; ++nout; }", "{ target = -1; ++nin; }", _census_pins),
     ("target = sorted index, not list index", "{ target = rg[lo - 1].id; ++nin; }",
      "{ target = lo - 1; ++nin; }", _census_pins),
     # compare
@@ -104,6 +107,7 @@ MUTANTS = [
     ("last mismatch index instead of first", "        if (mis) {\n            r.mismatches += 1;\n"
      "            if (r.first < 0) r.first = (int64_t)i;",
      "        if (mis) {\n            r.mismatches += 1;\n            r.first = (int64_t)i;", _compare_pins),
+    ("NaN count of got reads want", "r.nan_got += (uint64_t)na;", "r.nan_got += (uint64_t)nb;", _compare_pins),
     ("fp16 subnormal scale", "if (ex == 0) v = ldexp((double)fr, -24);", "if (ex == 0) v = ldexp((double)fr, -25);",
      _compare_pins),
     ("bf16 widened from the wrong bit", "uint32_t u = (uint32_t)h << 16;", "uint32_t u = (uint32_t)h << 15;",
