@@ -44,7 +44,7 @@ NOMINAL_HBM_GBPS = 7900.0   # GB300 HBM3e nominal; fractions are also given agai
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=3000)   # ~1.2 s timed: several clock samples inside it
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="kc", choices=["kc", "reference"])
     ap.add_argument("--variant", default="full", choices=["full", "152MB"])
@@ -118,7 +118,9 @@ class ClockSampler:
                 continue
         if not rows:
             return None
-        inside = [r for r in rows if t0 - 0.25 <= r[0] <= t1 + 0.25] or rows
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if len(inside) < 3:     # a short timed region: take the samples next to it too
+            inside = [r for r in rows if t0 - 0.25 <= r[0] <= t1 + 0.25] or rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({n for r in inside for n, v in zip(names, r[3]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(r[1] for r in inside),

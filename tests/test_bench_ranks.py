@@ -65,3 +65,18 @@ def test_reference_arm_works_on_rank_zero_only(monkeypatch, capsys):
     args = argparse.Namespace(seed=0, variant="full", steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_clock_summary_prefers_samples_inside_the_timed_region():
+    import bench
+    cs = bench.ClockSampler(0)
+    row = "0, {sm}, 2070, 900.00, 0x0, {hw}, Not Active, Not Active, {cap}"
+    cs.lines = [(9.5, row.format(sm=1000, hw="Not Active", cap="Not Active")),     # before: idle, lower clock
+                (10.1, row.format(sm=2070, hw="Not Active", cap="Active")),
+                (10.3, row.format(sm=2050, hw="Not Active", cap="Not Active")),
+                (10.5, row.format(sm=2070, hw="Not Active", cap="Not Active")),
+                (11.2, row.format(sm=1000, hw="Active", cap="Not Active"))]        # after
+    s = cs.summary(10.0, 11.0)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s = cs.summary(10.0, 10.2)                 # one sample inside: the neighbours within 0.25 s count too
+    assert s["samples"] == 2 and s["sm_mhz"] == 2060.0
