@@ -150,6 +150,31 @@ def test_scan_dense_pointers_many_chunks(ctx, page):
     assert ctx.sync() == kc.OK and (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
 
 
+def test_scan_page_mode_above_list_limit(ctx):
+    """More than 65536 pages: the fused scan's census tail takes chunks of
+    consecutive pages (page mode) instead of the list of flagged pages; hits,
+    counts and digests as the oracle's, and truncation keeps the first hits."""
+    MiB = W.MiB
+    sizes = [96 * MiB + 8, 64 * MiB - 40, 80 * MiB + 1234, 60 * MiB]
+    layout = W.Snapshot("page-mode", 4096, sizes, dtypes=[kc.RAW] * len(sizes))
+    snap, dev = G.device_snapshot(layout, W.tiny_fill, 7, p_ptr=0.02, p_zero=0.1)
+    assert sum(-(-s // 4096) for s in sizes) > 65536
+    win = W.default_window(snap.bases, snap.sizes)
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert rc == 0 and nin + nout > 100000
+    st, r = G.run_scan(ctx, snap, dev, win, cap=nin + nout)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][: nin + nout]) == G.hits_tuples(ohits)
+    oh, oz, _ = _oracle_digest(snap, 4096)
+    assert np.array_equal(r["hash"], oh) and np.array_equal(r["zero"], oz)
+    cap = 12345
+    st, r = G.run_scan(ctx, snap, dev, win, cap=cap)
+    assert ctx.sync() == kc.ETRUNC
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][:cap]) == G.hits_tuples(ohits[:cap])
+
+
 def test_census_standalone(ctx, tiny):
     snap, dev = tiny
     win = W.default_window(snap.bases, snap.sizes)
