@@ -4,6 +4,9 @@
   search), vectorised with numpy.
 - Every pointer the generator planted is found, with its target region.
 - Truncation keeps the true counts; overlapping ranges are rejected.
+- A region whose image is only a prefix (or nothing) is still a whole
+  target range: only the image is scanned, values anywhere in the region
+  are inside hits.
 """
 import numpy as np
 import pytest
@@ -110,3 +113,48 @@ def test_census_truncation_keeps_true_counts_and_overlap_rejected():
     bad[1] = bad[0] + 8                 # region 1 now starts inside region 0
     _, _, _, rc3 = oracle.census(snap.regions, bad, lo, hi)
     assert rc3 == 2
+
+
+def test_census_scan_prefix_and_target_only():
+    """Regions given as a prefix of their bytes (the oracle's `scan` lengths):
+    the region stays a whole half-open target range, only the prefix is read.
+    Region 1 passes its first 1 KiB of 8 KiB (its rest holds pointers that
+    must not be read), region 2 passes nothing (a target only); words of
+    region 0 point past region 1's prefix and into region 2."""
+    bases = [0x100000, 0x200000, 0x300000]
+    sizes = [4096, 8192, 4096]
+    full = [np.zeros(s, dtype=np.uint8) for s in sizes]
+    w0 = full[0].view("<u8")
+    w0[0] = 0x200000 + 5000          # inside region 1, past its scanned prefix
+    w0[1] = 0x200000 + 8191          # last byte of region 1
+    w0[2] = 0x200000 + 8192          # one past region 1: the window
+    w0[3] = 0x300000                 # region 2, never scanned itself
+    w0[4] = 0x300000 + 4095
+    w0[5] = 0x300000 + 4096          # one past region 2: the window
+    w0[6] = 0x100000 + 8             # region 0 itself
+    w1 = full[1].view("<u8")
+    w1[1] = 0x300000 + 16            # inside the prefix: found
+    w1[200] = 0x100000               # past the prefix (offset 1600): not read
+    w1[1000] = 0x300000 + 8          # past the prefix: not read
+    full[2].view("<u8")[:] = 0x100000   # target only: none of these is read
+    images = [full[0], full[1][:1024], full[2][:0]]
+    lo, hi = 0x80000, 0x380000
+    hits, nin, nout, rc = oracle.census(images, bases, lo, hi, sizes=sizes)
+    assert rc == 0
+    # brute force: a linear scan over every full range, words of the images only
+    brute = []
+    for i, img in enumerate(images):
+        for o in range(0, img.size - img.size % 8, 8):
+            v = int(img[o:o + 8].view("<u8")[0])
+            tgt = [k for k in range(3) if bases[k] <= v < bases[k] + sizes[k]]
+            if tgt:
+                brute.append((i, o, v, tgt[0]))
+            elif lo <= v < hi:
+                brute.append((i, o, v, -1))
+    assert _as_tuples(hits) == brute
+    assert brute[:7] == [(0, 0, 0x200000 + 5000, 1), (0, 8, 0x200000 + 8191, 1), (0, 16, 0x200000 + 8192, -1),
+                         (0, 24, 0x300000, 2), (0, 32, 0x300000 + 4095, 2), (0, 40, 0x300000 + 4096, -1),
+                         (0, 48, 0x100000 + 8, 0)]
+    assert (1, 8, 0x300000 + 16, 2) in brute and not any(b[0] == 1 and b[1] >= 1024 for b in brute)
+    assert not any(b[0] == 2 for b in brute)
+    assert (nin, nout) == (sum(1 for b in brute if b[3] >= 0), sum(1 for b in brute if b[3] == -1))

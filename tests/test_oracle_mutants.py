@@ -45,6 +45,7 @@ def _census_pins():
     TC.test_census_finds_every_planted_pointer()
     TC.test_census_llama_pointer_table()
     TC.test_census_truncation_keeps_true_counts_and_overlap_rejected()
+    TC.test_census_scan_prefix_and_target_only()
     for seed in (0, 1, 2):
         TC.test_census_matches_linear_scan(seed)
 
@@ -96,6 +97,8 @@ MUTANTS = [
     ("last word of a region skipped", "for (uint64_t o = 0; o + 8 <= lim; o += 8)",
      "for (uint64_t o = 0; o + 16 <= lim; o += 8)", _census_pins),
     ("outside hits counted as inside", "{ target = -1; ++nout; }", "{ target = -1; ++nin; }", _census_pins),
+    ("range end taken from the scanned prefix", "rg[k].end = base[k] + bytes[k];",
+     "rg[k].end = base[k] + (scan ? scan[k] : bytes[k]);", _census_pins),
     ("target = sorted index, not list index", "{ target = rg[lo - 1].id; ++nin; }",
      "{ target = lo - 1; ++nin; }", _census_pins),
     # compare
