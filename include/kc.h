@@ -172,6 +172,20 @@ KC_API kc_status kc_set_digest_shape(kc_ctx *ctx, int warps, int stages, int chu
 KC_API kc_status kc_get_digest_shape(kc_ctx *ctx, uint32_t page_bytes, uint64_t npages, int *warps,
                                      int *stages, int *chunk, int *ctas, int *lanes);
 
+/* kc_debug_stall_census: test hook for the bounded waits of kc_scan's
+ * census.  The census orders its hits with a decoupled look-back: each
+ * chunk of pages publishes its hit total and waits (bounded) for earlier
+ * chunks' totals, following the paper's rule that a failure is reported,
+ * never silently lost (Section "Memory Capture", paragraph "Ordering and
+ * crash safety").  After this call, the context's next kc_scan starts the
+ * chunk tickets at 1, so chunk 0 is never taken and never published, and
+ * bounds every look-back wait at `spin_limit` polls: a later chunk with
+ * hits gives up after the limit, the kernel finishes, and kc_sync reports
+ * KC_ETIMEOUT (that call's census outputs are incomplete; its digest is
+ * exact).  One-shot: the call after it runs normally.  KC_EINVAL if ctx
+ * is NULL or spin_limit is 0. */
+KC_API kc_status kc_debug_stall_census(kc_ctx *ctx, uint32_t spin_limit);
+
 /* kc_set_trace_events: `start` and `stop` (cudaEvent_t, or NULL to turn
  * tracing off) are recorded on the call's stream around the main kernel of
  * every following call: the digest kernel of kc_digest / kc_scan, the count
@@ -222,17 +236,29 @@ KC_API kc_status kc_census(kc_ctx *ctx, const kc_buf *allocs, int n, uint64_t wi
  * the caller's current device, with no context, and allocates nothing: its
  * scratch (region table, sorted ranges, per-64-KiB-chunk hit counts and
  * offsets, a status word) is one static device array of about 0.8 MiB in
- * the library image, which every GPU that loads the library holds until the
- * process exits.  Limits: n <= 1024 regions and at most 65536 chunks of
- * 64 KiB (ceil(bytes / 64 KiB) summed over the regions, i.e. about 4 GiB);
- * larger requests return KC_EINVAL before any work.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress), so make
- * it before any stream capture.  Every call on a device shares the array and
- * overwrites the previous call's contents: calls that may overlap on the GPU
- * (different streams, or different host threads with unordered streams)
- * race, so serialise them.  Truncation is not reported separately: the true
- * counts are written to d_counts, so n_inside + n_outside > cap means the
- * list was cut.  Returns KC_OK, KC_EINVAL, KC_EOVERLAP, KC_ECUDA or KC_EBUF. */
+ * the library's image.
+ * Set-up: CUDA loads a module's code and static data onto a device lazily,
+ * when first used, and that load takes device memory.  The first call on a
+ * device therefore does a one-time set-up -- it loads the array and every
+ * kernel a call launches (one empty launch each on `stream`) and looks up
+ * the array's device address -- after which the device holds the array
+ * until the process exits and calls load nothing.  kc_census_static(NULL,
+ * 0, 0, 0, NULL, 0, NULL, stream) does only that set-up and returns KC_OK;
+ * make it (or a first call) while device memory is still available.
+ * Limits: n <= 1024 regions and at most 65536 chunks of 64 KiB
+ * (ceil(bytes / 64 KiB) summed over the regions, i.e. about 4 GiB); larger
+ * requests return KC_EINVAL before any work.
+ * Not capturable: the call copies its tables from shared host memory, so
+ * inside a stream capture it returns KC_EINVAL and enqueues nothing.
+ * Every call on a device shares the array and overwrites the previous
+ * call's contents: calls that may overlap on the GPU (different streams, or
+ * different host threads with unordered streams) race, so serialise them.
+ * A race that the write pass detects (a chunk whose recount differs from
+ * its count) sets both counts to all-ones (UINT64_MAX), a value no census
+ * produces; not every race is detected.  Truncation is not reported
+ * separately: the true counts are written to d_counts, so n_inside +
+ * n_outside > cap means the list was cut.  Returns KC_OK, KC_EINVAL,
+ * KC_EOVERLAP, KC_ECUDA or KC_EBUF. */
 KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, uint64_t win_hi,
                                   kc_hit *d_hits, uint64_t cap, uint64_t *d_counts, void *stream);
 

@@ -130,7 +130,7 @@ __device__ __forceinline__ UnitSpan page_span(const Pages &u, uint64_t p, int ri
 // stops at the nearest inclusive prefix, adding the totals of the chunks
 // between it and c.
 __device__ __forceinline__ unsigned long long lookback(volatile unsigned long long *word, uint64_t c,
-                                                       uint32_t *status) {
+                                                       uint32_t *status, uint32_t spin_limit) {
     const uint32_t lane = lane_id();
     unsigned long long prefix = 0;
     int64_t base = (int64_t)c - 1;
@@ -152,7 +152,7 @@ __device__ __forceinline__ unsigned long long lookback(volatile unsigned long lo
                     missing |= (w[k] & ~LB_VALUE) == 0;
                 }
             }
-            if (!__any_sync(0xffffffffu, missing) || ++spins >= LB_SPIN_LIMIT) break;
+            if (!__any_sync(0xffffffffu, missing) || ++spins >= spin_limit) break;
         }
         if (__any_sync(0xffffffffu, missing)) {
             if (lane == 0) set_status(status, ST_TIMEOUT);
@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
                                                                     const uint32_t *__restrict__ nlist,
                                                                     kc_hit *__restrict__ hits, uint64_t cap,
                                                                     uint64_t *__restrict__ counts,
-                                                                    uint32_t *__restrict__ status) {
+                                                                    uint32_t *__restrict__ status,
+                                                                    uint32_t spin_limit) {
     __shared__ Range srg[SMEM_RANGES];
     __shared__ kc_hit stash[TAIL_WARPS][TAIL_STASH];
     __shared__ uint32_t freg[TAIL_CHUNK];
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
                 if (lane == 0) word[c] = LB_AGG;
             } else {
                 if (lane == 0) word[c] = LB_AGG | total;
-                prefix = lookback(word, c, status);
+                prefix = lookback(word, c, status, spin_limit);
                 if (lane == 0) word[c] = LB_PREFIX | (prefix + total);
             }
             if (lane == 0) {
@@ -402,8 +403,9 @@ uint64_t census_tail_words(uint64_t npages, int sms) {
 
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
                                uint32_t *list, kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status,
-                               int sms, cudaStream_t st) {
+                               int sms, uint32_t spin_limit, cudaStream_t st) {
     if (pg.npages == 0) return cudaSuccess;
+    if (spin_limit == 0) spin_limit = LB_SPIN_LIMIT;
     const uint64_t maxb = (uint64_t)sms * 2;
     if (pg.npages <= TAIL_LIST_MAX) {
         uint32_t *nlist = list + pg.npages;
@@ -412,14 +414,15 @@ cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         census_tail_kernel<<<(unsigned)maxb, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, pg.npages, 1, list, nlist,
-                                                                    cap ? hits : nullptr, cap, counts, status);
+                                                                    cap ? hits : nullptr, cap, counts, status,
+                                                                    spin_limit);
     } else {
         const uint32_t cp = tail_chunk_pages(pg.npages, sms);
         const uint64_t nchunks = (pg.npages + cp - 1) / cp;
         const uint64_t blocks = nchunks < maxb ? nchunks : maxb;
         census_tail_kernel<<<(unsigned)blocks, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, nchunks, cp, nullptr,
                                                                       nullptr, cap ? hits : nullptr, cap, counts,
-                                                                      status);
+                                                                      status, spin_limit);
     }
     count_launches(1);
     return cudaGetLastError();
@@ -624,5 +627,20 @@ cudaError_t launch_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint6
     return cudaGetLastError();
 }
 
+cudaError_t preload_census_kernels(cudaStream_t st) {
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, census_count_kernel)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, census_write_kernel)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, scan_u32_kernel)) != cudaSuccess)
+        return e;
+    Pages none{};
+    CensusArgs ca{};
+    census_count_kernel<<<1, CENSUS_THREADS, 0, st>>>(none, ca, nullptr, nullptr);
+    census_write_kernel<<<1, CENSUS_THREADS, 0, st>>>(none, ca, nullptr, nullptr, nullptr, 0, nullptr);
+    scan_u32_kernel<<<1, SCAN_THREADS, 0, st>>>(nullptr, nullptr, 0, nullptr);
+    count_launches(3);
+    return cudaGetLastError();
+}
 
 }  // namespace kc

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(512) digest_kernel(Pages pg, CensusArgs ca, ui
     {
         const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
         const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
-        for (uint64_t i = gt; i < aux.nzero; i += nt) aux.zero_words[i] = 0ull;
+        for (uint64_t i = gt; i < aux.nzero; i += nt) aux.zero_words[i] = i == 0 ? aux.first_ticket : 0ull;
         if (aux.counts && gt < 2) aux.counts[gt] = 0ull;
         for (uint64_t i = gt; i < aux.npf; i += nt) aux.pf_dst[i] = aux.pf_src[i];
     }

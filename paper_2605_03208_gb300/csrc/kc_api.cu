@@ -102,6 +102,7 @@ struct kc_ctx {
     DigestShape forced{0, 0, 0, 0, 0};
     cudaEvent_t trace_start = nullptr;   // caller-owned, recorded around main kernels
     cudaEvent_t trace_stop = nullptr;
+    uint32_t stall_census_spins = 0;     // test hook: see kc_debug_stall_census
 };
 
 namespace {
@@ -199,38 +200,6 @@ kc_status build_ranges(kc_ctx *c, const kc_buf *b, int n, std::vector<Range> &rg
     for (int i = 1; i < n; ++i)
         if (rg[i].base < rg[i - 1].end) return fail(c, KC_EOVERLAP, "regions %d and %d overlap", rg[i - 1].id, rg[i].id);
     return KC_OK;
-}
-
-CensusArgs make_census(const std::vector<Range> &rg, uint64_t win_lo, uint64_t win_hi) {
-    CensusArgs ca{};
-    ca.nranges = (int)rg.size();
-    uint64_t lo = ~0ull, hi = 0;
-    for (auto &r : rg) {
-        lo = std::min(lo, r.base);
-        hi = std::max(hi, r.end);
-    }
-    ca.span_lo = lo;
-    ca.span_len = hi - lo;
-    ca.win_lo = win_lo;
-    ca.win_len = win_hi > win_lo ? win_hi - win_lo : 0;
-    // high-32-bit pre-filter: the hull of the non-empty intervals
-    uint64_t plo = ~0ull, phi = 0;   // inclusive bounds
-    if (ca.span_len) {
-        plo = std::min(plo, ca.span_lo);
-        phi = std::max(phi, ca.span_lo + ca.span_len - 1);
-    }
-    if (ca.win_len) {
-        plo = std::min(plo, ca.win_lo);
-        phi = std::max(phi, ca.win_lo + ca.win_len - 1);
-    }
-    if (plo > phi) {   // nothing can be a hit
-        ca.pre_lo = 0xFFFFFFFFu;
-        ca.pre_span = 0;
-    } else {
-        ca.pre_lo = (uint32_t)(plo >> 32);
-        ca.pre_span = (uint32_t)(phi >> 32) - ca.pre_lo;
-    }
-    return ca;
 }
 
 void destroy_buf(TableBuf &b) {
@@ -358,7 +327,7 @@ kc_status page_tables(kc_ctx *c, const kc_buf *b, int n, uint32_t page, bool cen
                           if (census) {
                               std::vector<Range> rg;
                               if ((s = build_ranges(c, b, n, rg)) != KC_OK) return s;
-                              t.ca = make_census(rg, wlo, whi);
+                              t.ca = census_args(rg.data(), (int)rg.size(), wlo, whi);
                               put(parts[TP_RANGES], rg);
                           }
                           t.n = n;
@@ -582,6 +551,12 @@ KC_API kc_status kc_set_digest_shape(kc_ctx *c, int warps, int stages, int chunk
     return KC_OK;
 }
 
+KC_API kc_status kc_debug_stall_census(kc_ctx *c, uint32_t spin_limit) {
+    if (!c || spin_limit == 0) return KC_EINVAL;
+    c->stall_census_spins = spin_limit;
+    return KC_OK;
+}
+
 KC_API kc_status kc_set_trace_events(kc_ctx *c, void *start, void *stop) {
     if (!c) return KC_EINVAL;
     if ((start == nullptr) != (stop == nullptr)) return fail(c, KC_EINVAL, "give both trace events or neither");
@@ -623,6 +598,7 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
     unsigned long long *tail = nullptr;
     uint32_t *list = nullptr;
     DigestAux aux;
+    uint32_t spin_limit = 0;
     if (census) {
         // page_hits[P] | census tail: ticket + one word per chunk | list of flagged pages + count
         const uint64_t nwords = census_tail_words(P, c->sms);
@@ -634,6 +610,11 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
         list = reinterpret_cast<uint32_t *>(static_cast<char *>(scr) + hb + tb);
         aux.zero_words = tail;
         aux.nzero = nwords;
+        if (c->stall_census_spins) {   // one-shot test hook: chunk 0 is never taken
+            aux.first_ticket = 1;
+            spin_limit = c->stall_census_spins;
+            c->stall_census_spins = 0;
+        }
         aux.counts = d_counts;
     }
     if (d_page_first) {
@@ -650,7 +631,7 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
     }
     if (census)
         KC_CHECK(c, launch_census_tail(pg, t->ca, page_hits, tail, list, d_hits, cap, d_counts, status_word(c), c->sms,
-                                       st),
+                                       spin_limit, st),
                  "census tail");
     touch(c, t, st);
     return lost_status(c, t);

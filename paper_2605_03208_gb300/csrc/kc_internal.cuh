@@ -48,6 +48,43 @@ struct CensusArgs {
     uint32_t pre_lo, pre_span;
 };
 
+// Census parameters for the ranges rg[0..n) (sorted by base, disjoint) and
+// the window [win_lo, win_hi): the captured span, the window, and the
+// high-32-bit pre-filter over the hull of the non-empty intervals (every
+// value inside either interval passes it; pre_span 0 with pre_lo all-ones
+// when nothing can be a hit).  Used by both the context-based census and
+// the static one, so the two classify identically.
+inline CensusArgs census_args(const Range *rg, int n, uint64_t win_lo, uint64_t win_hi) {
+    CensusArgs ca{};
+    ca.nranges = n;
+    uint64_t lo = ~0ull, hi = 0;
+    for (int i = 0; i < n; ++i) {
+        lo = rg[i].base < lo ? rg[i].base : lo;
+        hi = rg[i].end > hi ? rg[i].end : hi;
+    }
+    ca.span_lo = lo;
+    ca.span_len = n > 0 ? hi - lo : 0;
+    ca.win_lo = win_lo;
+    ca.win_len = win_hi > win_lo ? win_hi - win_lo : 0;
+    uint64_t plo = ~0ull, phi = 0;   // inclusive bounds
+    if (ca.span_len) {
+        plo = ca.span_lo < plo ? ca.span_lo : plo;
+        phi = ca.span_lo + ca.span_len - 1 > phi ? ca.span_lo + ca.span_len - 1 : phi;
+    }
+    if (ca.win_len) {
+        plo = ca.win_lo < plo ? ca.win_lo : plo;
+        phi = ca.win_lo + ca.win_len - 1 > phi ? ca.win_lo + ca.win_len - 1 : phi;
+    }
+    if (plo > phi) {
+        ca.pre_lo = 0xFFFFFFFFu;
+        ca.pre_span = 0;
+    } else {
+        ca.pre_lo = (uint32_t)(plo >> 32);
+        ca.pre_span = (uint32_t)(phi >> 32) - ca.pre_lo;
+    }
+    return ca;
+}
+
 // Work description shared by the page-granular kernels.
 struct Pages {
     const Region *regions;
@@ -83,6 +120,7 @@ cudaError_t setup_dedup_kernels();
 struct DigestAux {
     unsigned long long *zero_words = nullptr;   // zeroed (census tail ticket + chunk words)
     uint64_t nzero = 0;
+    unsigned long long first_ticket = 0;        // zero_words[0] gets this instead (a test hook)
     uint64_t *counts = nullptr;                 // caller's census counts, zeroed
     const uint64_t *pf_src = nullptr;           // page offsets copied to the caller
     uint64_t *pf_dst = nullptr;
@@ -98,15 +136,22 @@ cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *h
 // census_tail_words(P, sms) words zeroed by the digest kernel; list: P + 1
 // u32 of scratch.
 uint64_t census_tail_words(uint64_t npages, int sms);
+// spin_limit: polls each look-back wait makes before it gives up (0 = the
+// built-in limit of a few seconds).
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
                                uint32_t *list, kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status,
-                               int sms, cudaStream_t st);
+                               int sms, uint32_t spin_limit, cudaStream_t st);
 cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
                                 uint64_t *counts, int sms, cudaStream_t st);
 cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca,
                                 const uint32_t *unit_hits, const uint64_t *unit_off,
                                 kc_hit *hits, uint64_t cap, uint32_t *status, int sms,
                                 cudaStream_t st);
+
+// Load the standalone census kernels (count, scan, write) on the current
+// device now -- each launched once with no work on `st` -- so that a later
+// call launches code that is already resident.
+cudaError_t preload_census_kernels(cudaStream_t st);
 
 // Single-CTA exclusive scan of n u32 values into u64 offsets; total -> *total.
 cudaError_t launch_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t *total,

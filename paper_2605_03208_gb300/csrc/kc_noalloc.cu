@@ -13,12 +13,20 @@
 // kc_census_static runs the same census kernels, but all of its scratch --
 // the region table, the sorted ranges, the per-chunk hit counts and their
 // offsets, a status word -- lives in one file-scope static device array that
-// is part of the library image: every GPU that loads the library holds it
-// (about 0.8 MiB) until the process exits, and no call allocates anything.
-// Host code cannot pass the array's name to a kernel (in host code it is a
-// host-side stand-in, not a device address), so the first call on each
-// device looks up its device address with cudaGetSymbolAddress while that
-// device is current, and every later call on that device reuses it.
+// is part of this file's module: a device holds it (about 0.8 MiB) from the
+// moment the module is loaded there until the process exits, and no call
+// allocates anything.  Host code cannot pass the array's name to a kernel
+// (in host code it is a host-side stand-in, not a device address), so the
+// set-up of each device looks up its device address with
+// cudaGetSymbolAddress while that device is current, and every later call
+// on that device reuses it.
+//
+// Module loading is lazy by default in CUDA: a module's code and static
+// data are put on the device when first used, which itself takes device
+// memory.  The set-up therefore also loads every kernel a census call
+// launches (one launch each with no work), so that calls made after it load
+// nothing.  The set-up runs on the first call on a device, or explicitly
+// with kc_census_static(NULL, 0, ...), which does only the set-up.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,10 +53,22 @@ constexpr size_t NA_BYTES = NA_OFF_STATUS + 256;
 
 }  // namespace
 
-// The scratch itself: one copy per device that loads this library.
+// The scratch itself: one copy per device on which this module is loaded.
 static __device__ __align__(256) unsigned char g_census_scratch[NA_BYTES];
 
 namespace {
+
+// Last kernel of a call: if the write pass found a chunk whose recount
+// differs from its first count -- which happens when another call
+// overwrote the shared scratch in between -- both counts become all-ones,
+// a value no census can produce, so the caller sees that the call's hits
+// are not to be trusted.
+__global__ void census_static_finish_kernel(const uint32_t *__restrict__ status, uint64_t *__restrict__ counts) {
+    if (status && counts && (*status & ST_INTERNAL)) {
+        counts[0] = ~0ull;
+        counts[1] = ~0ull;
+    }
+}
 
 struct DeviceScratch {
     std::once_flag once;
@@ -59,14 +79,24 @@ struct DeviceScratch {
 
 DeviceScratch g_dev[NA_MAX_DEVICES];
 
-// One-time set-up on the current device: the array's device address and
-// the SM count.  Neither allocates.
-DeviceScratch *scratch_for(int device) {
+// One-time set-up on the current device: the array's device address, the
+// SM count, and every kernel of the call loaded (empty launches on `st`).
+// None of it allocates once the module is loaded; loading it is the one
+// moment device memory is taken.
+DeviceScratch *scratch_for(int device, cudaStream_t st) {
     DeviceScratch &d = g_dev[device];
-    std::call_once(d.once, [&d, device]() {
+    std::call_once(d.once, [&d, device, st]() {
         void *p = nullptr;
+        cudaFuncAttributes fa;
         d.err = cudaGetSymbolAddress(&p, g_census_scratch);
         if (d.err == cudaSuccess) d.err = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, device);
+        if (d.err == cudaSuccess) d.err = cudaFuncGetAttributes(&fa, census_static_finish_kernel);
+        if (d.err == cudaSuccess) {
+            census_static_finish_kernel<<<1, 1, 0, st>>>(nullptr, nullptr);
+            count_launches(1);
+            d.err = cudaGetLastError();
+        }
+        if (d.err == cudaSuccess) d.err = preload_census_kernels(st);
         if (d.err == cudaSuccess) d.ptr = static_cast<unsigned char *>(p);
         else cudaGetLastError();
     });
@@ -85,47 +115,15 @@ std::mutex g_host_lock;
 Region g_h_regions[NA_MAX_REGIONS];
 Range g_h_ranges[NA_MAX_REGIONS];
 
-// Census parameters for the sorted ranges: the captured span, the window,
-// and the conservative high-32-bit pre-filter over their hull (the same
-// rule the context-based census uses).
-CensusArgs static_census_args(const Range *rg, int n, uint64_t win_lo, uint64_t win_hi) {
-    CensusArgs ca{};
-    ca.nranges = n;
-    uint64_t lo = ~0ull, hi = 0;
-    for (int i = 0; i < n; ++i) {
-        lo = std::min(lo, rg[i].base);
-        hi = std::max(hi, rg[i].end);
-    }
-    ca.span_lo = lo;
-    ca.span_len = hi - lo;
-    ca.win_lo = win_lo;
-    ca.win_len = win_hi > win_lo ? win_hi - win_lo : 0;
-    uint64_t plo = ~0ull, phi = 0;
-    if (ca.span_len) {
-        plo = std::min(plo, ca.span_lo);
-        phi = std::max(phi, ca.span_lo + ca.span_len - 1);
-    }
-    if (ca.win_len) {
-        plo = std::min(plo, ca.win_lo);
-        phi = std::max(phi, ca.win_lo + ca.win_len - 1);
-    }
-    if (plo > phi) {
-        ca.pre_lo = 0xFFFFFFFFu;
-        ca.pre_span = 0;
-    } else {
-        ca.pre_lo = (uint32_t)(plo >> 32);
-        ca.pre_span = (uint32_t)(phi >> 32) - ca.pre_lo;
-    }
-    return ca;
-}
-
 }  // namespace
 
 extern "C" {
 
 KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, uint64_t win_hi, kc_hit *d_hits,
                                   uint64_t cap, uint64_t *d_counts, void *stream) {
-    if (!allocs || n < 1 || n > NA_MAX_REGIONS || !d_counts || (cap && !d_hits)) return KC_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool setup_only = allocs == nullptr && n == 0;
+    if (!setup_only && (!allocs || n < 1 || n > NA_MAX_REGIONS || !d_counts || (cap && !d_hits))) return KC_EINVAL;
     std::lock_guard<std::mutex> hold(g_host_lock);
     Region *regions = g_h_regions;
     Range *ranges = g_h_ranges;
@@ -146,14 +144,24 @@ KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, 
     for (int i = 1; i < n; ++i)
         if (ranges[i].base < ranges[i - 1].end) return KC_EOVERLAP;
 
+    // The host tables above are shared by every call and copied with plain
+    // asynchronous copies: a captured copy would read them again at every
+    // replay, after later calls have rewritten them, so capture is refused.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return KC_ECUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return KC_EINVAL;
+
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= NA_MAX_DEVICES) {
         cudaGetLastError();
         return KC_ECUDA;
     }
-    DeviceScratch *ds = scratch_for(device);
+    DeviceScratch *ds = scratch_for(device, st);
     if (!ds) return KC_ECUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (setup_only) return KC_OK;
     Region *d_regions = reinterpret_cast<Region *>(ds->ptr + NA_OFF_REGIONS);
     Range *d_ranges = reinterpret_cast<Range *>(ds->ptr + NA_OFF_RANGES);
     uint32_t *unit_hits = reinterpret_cast<uint32_t *>(ds->ptr + NA_OFF_HITS);
@@ -165,7 +173,7 @@ KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, 
     // Every count the kernels accumulate starts at zero: the caller's two
     // counters and the status word; unit_hits is written whole by the count
     // kernel and unit_off by the scan.
-    CensusArgs ca = static_census_args(ranges, n, win_lo, win_hi);
+    CensusArgs ca = census_args(ranges, n, win_lo, win_hi);
     ca.ranges = d_ranges;
     Pages u;
     u.regions = d_regions;
@@ -187,6 +195,9 @@ KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, 
             cudaGetLastError();
             return KC_ECUDA;
         }
+        census_static_finish_kernel<<<1, 1, 0, st>>>(status, d_counts);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) return KC_ECUDA;
     }
     return any_lost ? KC_EBUF : KC_OK;
 }

@@ -31,7 +31,7 @@ ESIZE = {U8: 1, RAW: 1, I32: 4, F16: 2, BF16: 2, F32: 4}
 
 # Names declared in include/kc.h (the ABI surface).
 EXPORTS = ["kc_version", "kc_launch_count", "kc_status_name", "kc_last_error", "kc_create", "kc_destroy", "kc_sync",
-           "kc_buf_status", "kc_set_digest_shape", "kc_set_trace_events", "kc_get_digest_shape", "kc_page_count",
+           "kc_buf_status", "kc_set_digest_shape", "kc_debug_stall_census", "kc_set_trace_events", "kc_get_digest_shape", "kc_page_count",
            "kc_digest", "kc_census", "kc_scan", "kc_dedup", "kc_restore", "kc_compare",
            "kc_census_static", "kc_batch_run", "kc_poll_flags"]
 
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = False):
     L.kc_buf_status.argtypes = [vp, i32]
     L.kc_set_digest_shape.restype = st
     L.kc_set_digest_shape.argtypes = [vp, i32, i32, i32, i32]
+    L.kc_debug_stall_census.restype = st
+    L.kc_debug_stall_census.argtypes = [vp, u32]
     L.kc_set_trace_events.restype = st
     L.kc_set_trace_events.argtypes = [vp, vp, vp]
     L.kc_get_digest_shape.restype = st
@@ -208,6 +210,12 @@ class Context:
 
     def set_digest_shape(self, warps=0, stages=0, chunk=0, lanes=0):
         return self._check(self.lib.kc_set_digest_shape(self.h, warps, stages, chunk, lanes), (OK,))
+
+    def debug_stall_census(self, spin_limit: int):
+        """kc_debug_stall_census: the next scan's census leaves its first
+        chunk unpublished and bounds each look-back wait at spin_limit polls
+        (a test of the bounded wait; kc_sync then reports KC_ETIMEOUT)."""
+        return self._check(self.lib.kc_debug_stall_census(self.h, spin_limit), (OK,))
 
     def set_trace_events(self, start=None, stop=None):
         """Record torch.cuda.Event objects around the main kernel of later calls.
@@ -329,7 +337,10 @@ class FlagPoller:
 
 def census_static(regions, win_lo, win_hi, hits_out, cap, counts_out, stream=None) -> int:
     """kc_census_static: the census without a context and without allocating
-    (scratch in a static device array; see include/kc.h).  Returns the status."""
+    (scratch in a static device array; see include/kc.h).  regions None: the
+    one-time set-up of the current device only.  Returns the status."""
+    if regions is None:
+        return int(load().kc_census_static(None, 0, 0, 0, None, 0, None, _stream(stream)))
     b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
     return int(load().kc_census_static(b, len(b), win_lo, win_hi, _ptr(hits_out), cap,
                                        _ptr(counts_out), _stream(stream)))

@@ -115,3 +115,27 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.startswith("ok KC_E")
+
+
+def test_census_static_argument_checks_are_host_only():
+    """kc_census_static validates on the host before touching a device: the
+    region-count and chunk limits, empty or misaligned regions and
+    overlapping ranges are refused without any CUDA call (these addresses
+    are never dereferenced)."""
+    lib = kc.load()
+    counts = 0x7000_0000_0000     # never written: every call below is refused first
+    cases = [
+        ([(0x10000 + 4096 * i, 4096) for i in range(1025)], kc.EINVAL),           # 1025 regions
+        ([(0x10_0000_0000, 4 * 2**30 + 65536)], kc.EINVAL),                        # 65537 chunks
+        ([(0x10_0000_0000, 2**32), (0x20_0000_0000, 1)], kc.EINVAL),              # 65537 chunks over two
+        ([(0x10000, 0)], kc.EINVAL),                                               # empty region
+        ([(0x10008, 64)], kc.EINVAL),                                              # not 16-byte aligned
+        ([(0x10000, 8192), (0x11000, 64)], kc.EOVERLAP),                          # overlapping ranges
+    ]
+    for regions, want in cases:
+        b = kc.bufs(regions)
+        assert lib.kc_census_static(b, len(b), 0, 0, None, 0, counts, 0) == want, regions
+    b = kc.bufs([(0x10000, 64)])
+    assert lib.kc_census_static(b, 1, 0, 0, None, 0, None, 0) == kc.EINVAL       # no counts output
+    assert lib.kc_census_static(b, 1, 0, 0, None, 5, counts, 0) == kc.EINVAL     # cap without hits
+    assert lib.kc_census_static(None, 1, 0, 0, None, 0, counts, 0) == kc.EINVAL  # no regions, n = 1

@@ -173,6 +173,34 @@ def test_scan_page_mode_above_list_limit(ctx):
     assert ctx.sync() == kc.ETRUNC
     assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
     assert G.hits_tuples(r["hits"][:cap]) == G.hits_tuples(ohits[:cap])
+    # the bounded look-back wait in page mode: chunk 0 never published
+    ctx.debug_stall_census(2000)
+    st, r = G.run_scan(ctx, snap, dev, win, cap=nin + nout)
+    assert st == kc.OK and ctx.sync() == kc.ETIMEOUT
+    assert np.array_equal(r["hash"], oh)
+
+
+def test_scan_census_bounded_wait_times_out(ctx):
+    """The census tail's look-back waits are bounded: with the test hook, the
+    first chunk of flagged pages is never published and every wait is cut
+    at 2000 polls; the chunks behind it give up, the kernel finishes and
+    kc_sync reports KC_ETIMEOUT (the digest of that call is still exact).
+    The context stays usable: the next scan is exact again."""
+    layout = W.tiny_layout(3, n=12, total=6 * W.MiB)
+    snap, dev = G.device_snapshot(layout, W.tiny_fill, 3, p_ptr=0.6, p_zero=0.1)
+    win = W.default_window(snap.bases, snap.sizes)
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    oh, oz, _ = _oracle_digest(snap, 4096)
+    ctx.debug_stall_census(2000)
+    st, r = G.run_scan(ctx, snap, dev, win, page_bytes=4096)
+    assert st == kc.OK and ctx.sync() == kc.ETIMEOUT
+    assert np.array_equal(r["hash"], oh) and np.array_equal(r["zero"], oz)
+    st, r = G.run_scan(ctx, snap, dev, win, page_bytes=4096)
+    assert ctx.sync() == kc.OK
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][: nin + nout]) == G.hits_tuples(ohits)
+    with pytest.raises(kc.KcError):
+        ctx.debug_stall_census(0)
 
 
 def test_census_standalone(ctx, tiny):

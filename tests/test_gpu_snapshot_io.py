@@ -1,7 +1,8 @@
 """GPU tests of snapshots on disk and of the byte-diff report: a saved
 snapshot restores byte for byte (into fresh regions and VA-faithfully into
 the original ones), its page table, digests and census equal the oracle's,
-and the byte-diff report equals numpy's."""
+and the byte-diff report equals the oracle's byte-exact comparison (and
+a direct count of the differing bytes)."""
 from __future__ import annotations
 
 import os
@@ -88,5 +89,8 @@ def test_byte_diff_report(ctx):
         d = int((a != b).sum())
         expect.append((d, 100.0 * d / n, int(np.nonzero(a != b)[0][0]) if d else -1))
     rep = V.byte_diff(ctx, got, want)
-    for r, (d, pct, first) in zip(rep, expect):
-        assert (r["differing"], r["first"]) == (d, first) and r["percent"] == pytest.approx(pct)
+    for r, (d, pct, first), (ga, n), (wb, _) in zip(rep, expect, got, want):
+        # the oracle's byte-exact comparison (KC_RAW, zero tolerance) of the same bytes
+        o = oracle.compare(ga.cpu().numpy(), wb.cpu().numpy(), oracle.DT_RAW)
+        assert (r["differing"], r["first"]) == (int(o["mismatches"]), int(o["first"])) == (d, first)
+        assert r["percent"] == pytest.approx(100.0 * int(o["mismatches"]) / n) == pytest.approx(pct)
