@@ -160,14 +160,20 @@ KC_API kc_status kc_sync(kc_ctx *ctx, void *stream);
  * a region list (KC_OK, or KC_EBUF when it was lost).  -1 if out of range. */
 KC_API int kc_buf_status(const kc_ctx *ctx, int i);
 
-/* kc_set_digest_shape: pin the digest kernel's launch shape for this
- * context: `warps` per CTA (1..16), ring `stages` per warp (2..8), `chunk`
- * bytes per page per stage (multiple of 128, 256..8192), and `lanes` XXH64
- * accumulators per thread (1: 4 threads and 8 pages per warp; 2: 2 threads
- * and 16 pages per warp).  All four 0 restores the built-in choice.  The
- * shape changes speed only, never results.  KC_EINVAL if out of range.
+/* kc_set_digest_shape: pin the digest's launch shape for this context.
+ * The digest kernel (kc_digest, kc_scan) runs CTAs of one producer warp,
+ * which streams pages into shared memory with bulk copies, and `warps` hash
+ * warps (1..16) of 8 pages each (one XXH64 accumulator per thread); each
+ * hash warp owns a ring of `stages` (2..8) stages of `chunk` bytes per page
+ * (multiple of 128, 256..8192).  The batched kernel (kc_batch_run) reads
+ * the same three numbers as its warps per CTA, per-warp ring stages and
+ * chunk.  `lanes` must be 0 or 1 (one accumulator per thread).  All four 0
+ * restores the built-in choice.  The shape changes speed only, never
+ * results.  KC_EINVAL if out of range or if the rings do not fit a CTA's
+ * shared memory.
  * kc_get_digest_shape: the shape a digest of `npages` pages of
- * `page_bytes` would use now, and its grid size (`ctas`). */
+ * `page_bytes` would use now (`warps` = hash warps), and its grid size
+ * (`ctas`). */
 KC_API kc_status kc_set_digest_shape(kc_ctx *ctx, int warps, int stages, int chunk, int lanes);
 KC_API kc_status kc_get_digest_shape(kc_ctx *ctx, uint32_t page_bytes, uint64_t npages, int *warps,
                                      int *stages, int *chunk, int *ctas, int *lanes);

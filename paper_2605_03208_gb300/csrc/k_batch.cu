@@ -136,6 +136,10 @@ cudaError_t setup_batch_kernels() {
     return setup_batch_one<1024>();
 }
 
+size_t batch_smem_bytes(const DigestShape &s) {
+    return (size_t)s.warps * s.stages * BATCH_PPW * ((size_t)s.chunk + 32);
+}
+
 cudaError_t launch_batch(const BatchJob *jobs, int njobs, uint32_t *left, const BatchRange *ranges, int nranges,
                          uint64_t nitems, uint32_t page, const DigestShape &shape, double atol, double rtol,
                          uint32_t *ctr, int sms, cudaStream_t st) {
@@ -145,7 +149,7 @@ cudaError_t launch_batch(const BatchJob *jobs, int njobs, uint32_t *left, const 
     if (e != cudaSuccess || nitems == 0) return e;
     uint32_t log2page = 0;
     while ((1u << log2page) < page) ++log2page;
-    const size_t smem = (size_t)shape.warps * shape.stages * BATCH_PPW * (shape.chunk + 32);
+    const size_t smem = batch_smem_bytes(shape);
     const dim3 grid(shape.ctas), block(32 * shape.warps);
     switch (shape.chunk) {
     case 512:

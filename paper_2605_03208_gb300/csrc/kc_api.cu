@@ -372,17 +372,13 @@ struct Trace {
 uint32_t *status_word(kc_ctx *c) { return reinterpret_cast<uint32_t *>(&c->d_misc[0]); }
 uint32_t *task_counter(kc_ctx *c) { return reinterpret_cast<uint32_t *>(&c->d_misc[1]); }
 
-// Built-in digest shape.  XXH64 is a serial chain per lane and every warp
-// owns 8 pages at a time (one lane per thread: measured faster than two
-// lanes per thread on every workload tried), so a page started late finishes
-// late: keep every task resident at once when that fits (up to 24 warps per
-// SM), in CTAs of 2 warps, then give each warp the first ring in the
-// preference list that fits its share of the SM's shared memory.  A ring of
-// two 1 KiB stages comes before deeper rings of 1 KiB or smaller chunks: on
-// 64 KiB pages with ~5 warps per SM it measured ~5% faster than four stages
-// (the warps are bound by their own instruction latency, and a deeper ring
-// only adds copies in flight).
-DigestShape pick_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
+// Shape of the batched kernel (k_batch.cu), whose warps each stream their
+// own pages through a per-warp ring.  XXH64 is a serial chain per lane and
+// every warp owns 8 pages at a time, so a page started late finishes late:
+// keep every item resident at once when that fits (up to 24 warps per SM),
+// in CTAs of 2 warps, then give each warp the first ring in the preference
+// list that fits its share of the SM's shared memory.
+DigestShape pick_batch_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
     const size_t smem_sm = c->smem_per_sm ? c->smem_per_sm : 228 * 1024;
     DigestShape s = c->forced;
     if (s.lanes == 0) s.lanes = 1;
@@ -411,7 +407,7 @@ DigestShape pick_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
         }
     }
     if ((uint32_t)s.chunk > page) s.chunk = (int)page;
-    const size_t cta_smem = digest_smem_bytes(s);
+    const size_t cta_smem = batch_smem_bytes(s);
     uint64_t ctas_per_sm = smem_sm / (cta_smem + 1024);
     const uint64_t by_threads = 2048 / (32 * s.warps);
     if (ctas_per_sm > by_threads) ctas_per_sm = by_threads;
@@ -419,6 +415,57 @@ DigestShape pick_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
     if (ctas_per_sm < 1) ctas_per_sm = 1;
     uint64_t grid = (tasks + s.warps - 1) / s.warps;
     if (grid > ctas_per_sm * c->sms) grid = ctas_per_sm * c->sms;
+    s.ctas = (int)(grid ? grid : 1);
+    return s;
+}
+
+// Shape of the digest kernel (k_digest.cu): hash warps per CTA (`warps`,
+// plus as many loader warps), ring stages and chunk bytes per page and
+// stage, grid.  Every task (8 pages) runs on one hash warp from start to
+// end, and XXH64's chains are serial, so a task started late finishes late:
+// give every SM one CTA with enough hash warps for its share of the tasks,
+// up to 8 (two per SM
+// sub-partition: more only queue behind each other on the same issue
+// slots); larger snapshots reuse the warps through the ticket counter.
+// Then the first ring in the preference list that fits the SM's shared
+// memory.  Measured on the llama-shaped snapshot (6,327 pages of 64 KiB, 6
+// hash warps per SM): 2 KiB x 2 stages 91.6 us, 1 KiB x 3 93.2 us, 1 KiB x 4
+// 96.4 us, 512 B x 4 115 us; on the 30 GiB MoE pool (2 MiB pages, 8 hash
+// warps): 1 KiB x 3 5.09 ms (2 KiB stages do not fit 8 warps).
+DigestShape pick_digest_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
+    const size_t smem_sm = c->smem_per_sm ? c->smem_per_sm : 228 * 1024;
+    DigestShape s = c->forced;
+    s.lanes = 1;
+    const uint64_t tasks = (npages + 7) / 8;
+    const uint64_t sms = (uint64_t)c->sms;
+    if (s.warps == 0) {
+        uint64_t per_sm = (tasks + sms - 1) / sms;
+        if (per_sm < 1) per_sm = 1;
+        if (per_sm > 8) per_sm = 8;
+        s.warps = (int)per_sm;
+        static const int pref[][2] = {{2048, 2}, {1024, 3}, {1024, 4}, {512, 4}, {1024, 2},
+                                      {512, 3},  {512, 2},  {256, 4},  {256, 3}, {256, 2}};
+        s.chunk = 256;
+        s.stages = 2;
+        for (auto &pc : pref) {
+            if ((uint32_t)pc[0] > page) continue;
+            DigestShape t{s.warps, pc[1], pc[0], 1, 1};
+            if (digest_smem_bytes(t) + 1024 <= smem_sm) {
+                s.chunk = pc[0];
+                s.stages = pc[1];
+                break;
+            }
+        }
+    }
+    if (s.warps > digest_max_hash_warps()) s.warps = digest_max_hash_warps();
+    if ((uint32_t)s.chunk > page) s.chunk = (int)page;
+    uint64_t per_sm = smem_sm / (digest_smem_bytes(s) + 1024);
+    const uint64_t by_threads = 2048 / (64 * s.warps);
+    if (per_sm > by_threads) per_sm = by_threads;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (tasks + s.warps - 1) / s.warps;
+    if (grid < sms && tasks >= sms) grid = sms;   // every SM works, some hash warps idle
+    if (grid > per_sm * sms) grid = per_sm * sms;
     s.ctas = (int)(grid ? grid : 1);
     return s;
 }
@@ -542,12 +589,12 @@ KC_API kc_status kc_set_digest_shape(kc_ctx *c, int warps, int stages, int chunk
         return KC_OK;
     }
     if (warps < 1 || warps > 16 || stages < 2 || stages > 8 || chunk < 256 || chunk > 8192 || (chunk % 128) ||
-        (lanes != 1 && lanes != 2))
+        (lanes != 0 && lanes != 1))
         return fail(c, KC_EINVAL, "digest shape out of range (warps %d, stages %d, chunk %d, lanes %d)", warps, stages,
                     chunk, lanes);
-    DigestShape s{warps, stages, chunk, 1, lanes};
+    DigestShape s{warps, stages, chunk, 1, 1};
     if (digest_smem_bytes(s) > 227 * 1024) return fail(c, KC_EINVAL, "digest shape needs too much shared memory");
-    c->forced = DigestShape{warps, stages, chunk, 0, lanes};
+    c->forced = DigestShape{warps, stages, chunk, 0, 1};
     return KC_OK;
 }
 
@@ -568,7 +615,7 @@ KC_API kc_status kc_set_trace_events(kc_ctx *c, void *start, void *stop) {
 KC_API kc_status kc_get_digest_shape(kc_ctx *c, uint32_t page_bytes, uint64_t npages, int *warps, int *stages,
                                      int *chunk, int *ctas, int *lanes) {
     if (!c || !pow2_page(page_bytes)) return KC_EINVAL;
-    DigestShape s = pick_shape(c, page_bytes, npages);
+    DigestShape s = pick_digest_shape(c, page_bytes, npages);
     if (warps) *warps = s.warps;
     if (stages) *stages = s.stages;
     if (chunk) *chunk = s.chunk;
@@ -593,7 +640,7 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
     if (s != KC_OK) return s;
     const uint64_t P = t->units;
     const Pages pg = make_pages(t->regions(), n, P, page_bytes);
-    const DigestShape shape = pick_shape(c, page_bytes, P);
+    const DigestShape shape = pick_digest_shape(c, page_bytes, P);
     uint32_t *page_hits = nullptr;
     unsigned long long *tail = nullptr;
     uint32_t *list = nullptr;
@@ -894,7 +941,7 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
     if (s != KC_OK) return s;
     // digest shape: the persistent grid fills the GPU; warps take digest
     // items and comparison items alike
-    DigestShape shape = pick_shape(c, page_bytes, t->items * 8);
+    DigestShape shape = pick_batch_shape(c, page_bytes, t->items * 8);
     shape.lanes = 1;
     shape.ctas = (int)std::min<uint64_t>((uint64_t)shape.ctas, std::max<uint64_t>(1, t->items));
     KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");

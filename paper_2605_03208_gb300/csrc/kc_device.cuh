@@ -41,6 +41,81 @@ __device__ __forceinline__ void cp_async_wait(int n) {
     }
 }
 
+// ---- mbarriers and bulk copies (shared memory of this CTA) --------------------
+//
+// A stage of a ring is guarded by two mbarriers with one arrival each:
+// "full" (the producer arrives with the stage's byte count; the bulk copies
+// complete the transaction) and "empty" (the consumer arrives when it has
+// read the stage).  Waits poll try_wait with a phase parity and give up
+// after `limit` polls or when *abort is set, so no wait can hang a kernel.
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Makes initialised barriers visible to the asynchronous (bulk copy) proxy.
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// As mbar_test, but a thread whose phase has not completed is suspended by
+// the hardware until it completes or about `hint_ns` nanoseconds pass, so a
+// waiting warp takes no issue slots from the warps doing the work.
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+// Wait until the phase of parity `parity` has completed; false if the wait
+// gave up (after `limit` suspended polls of up to ~64 us each, or when
+// *abort was set by another warp).
+constexpr uint32_t MBAR_SLEEP_NS = 1u << 16;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit,
+                                          const volatile uint32_t *abort) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_test_sleep(bar, parity, MBAR_SLEEP_NS)) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+// The barrier's current phase also waits for every cp.async this thread has
+// issued so far: its pending count rises by one now and falls by one when
+// those copies have landed.
+__device__ __forceinline__ void mbar_track_cp_async(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// One bulk copy global -> this CTA's shared memory, completing `bytes` of
+// the barrier's transaction.  dst and src 16-byte aligned, bytes a multiple
+// of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits) {
     if (status) atomicOr(status, bits);
 }

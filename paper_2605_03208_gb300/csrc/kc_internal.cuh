@@ -96,14 +96,18 @@ struct Pages {
 
 // Digest kernel shape (chosen by the host planner or the autotuner).
 struct DigestShape {
-    int warps;        // warps per CTA
-    int stages;       // ring depth per warp
-    int chunk;        // bytes per page per stage (multiple of 32, <= page)
+    int warps;        // hash warps per CTA (digest kernel: plus as many loader warps)
+    int stages;       // ring depth per hash warp
+    int chunk;        // bytes per page per stage (multiple of 128, <= page)
     int ctas;         // grid size
-    int lanes;        // XXH64 lanes per thread: 1 (8 pages per warp) or 2 (16)
+    int lanes;        // XXH64 lanes per thread: always 1 (8 pages per warp)
 };
 
+// Dynamic shared memory of a CTA of the digest kernel (warps = hash warps)
+// and of the batched kernel (warps = warps of the CTA).
 size_t digest_smem_bytes(const DigestShape &s);
+size_t batch_smem_bytes(const DigestShape &s);
+int digest_max_hash_warps();
 
 // Process-wide count of kernels launched by this library (every launcher
 // adds its launches); read by kc_launch_count().

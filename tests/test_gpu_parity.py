@@ -54,10 +54,15 @@ def test_digest_tiny_bit_exact(ctx, tiny, S):
 
 
 @pytest.mark.parametrize("shape", [(1, 2, 256, 1), (2, 3, 512, 1), (4, 4, 1024, 1), (4, 2, 2048, 1),
-                                   (3, 5, 384, 1), (16, 2, 256, 1), (1, 2, 256, 2), (2, 4, 1024, 2),
-                                   (3, 3, 640, 2), (2, 2, 2048, 2)])
+                                   (3, 5, 384, 1), (16, 2, 256, 1), (8, 3, 1024, 1), (6, 3, 640, 1),
+                                   (1, 3, 8192, 1), (2, 2, 4096, 0), (5, 8, 512, 1)])
 def test_digest_forced_shapes(ctx, tiny, shape):
+    """Hash warps per CTA (plus the producer warp), ring stages and chunk
+    bytes change speed only: one stage in flight to deep rings, chunks that
+    are and are not a compile-time size, one to sixteen hash warps."""
     snap, dev = tiny
+    with pytest.raises(kc.KcError):
+        ctx.set_digest_shape(2, 4, 1024, 2)    # two lanes per thread: no longer offered
     ctx.set_digest_shape(*shape)
     try:
         st, h, z, pf = G.run_digest(ctx, snap, dev, 65536)
