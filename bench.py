@@ -1,24 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the snapshot path on one GB300 (or N replicas).
 
-One step = one pass of the whole path over the llama.cpp-shaped synthetic
-snapshot (400 regions, ~0.39 GiB, 64 KiB pages) and its fp32 logits pairs:
+Headline workload: the 30 GiB MoE weight pool (64 experts x 24 layers x 20
+MiB of bf16, 2% duplicate pages, plus the int64 array of the 1536 expert
+base VAs; 2 MiB pages) and its bf16 [4096, 7168] output pairs.  One step is
+one pass of the whole path over it:
   kc_scan    fused XXH64 page digest + zero flags + pointer census
-  kc_dedup   radix sort, byte verification, page table, blob pack
+  kc_dedup   grouping, byte verification, page table, blob pack
   kc_restore blobs written back at their VA offsets (in place: the regions
              are rewritten with identical bytes, so every step sees the same
              input)
-  kc_compare fp32 [8, 32000] x 2 pairs, FP64 error maxima
+  kc_compare bf16 [4096, 7168] x 2 pairs, FP64 error maxima (second stream)
 The timed region replays the step captured once as a CUDA graph (the
 library's calls are capture-safe once their tables are cached); a separate
 instrumented pass gives the per-call split and the digest kernel's time.
 value = algorithmic bytes of the step / device time of the step:
   2N (scan read + restore write) + 3U (pack read/write, restore read, U =
   unique non-zero page bytes) + 2C (compare read).
-Inputs (0.39 GiB) are larger than the 129 MB L2, so no flush is needed.
+Inputs (30 GiB) are far larger than the 129 MB L2, so no flush is needed.
+e2e: the same step through the C ABI with the snapshot ingested every step
+from a pinned host image (kc_restore reading host memory), the comparison
+inputs copied in and the outputs read back.
+Secondary sections: the llama.cpp-shaped snapshot (400 regions, 64 KiB
+pages; full and "152MB" variants), the batched form (4096 jobs), the served
+form (Poisson requests), snapshots on disk.
 
---impl reference times the CPU oracle (oracle/kc_oracle.c, single-threaded)
-on the same workload and metric.
+--impl reference times the CPU oracle (oracle/kc_oracle.c, single thread, as
+it stands) on host samples of the same workload, metric and unit.
 """
 from __future__ import annotations
 
@@ -30,6 +38,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -39,25 +48,37 @@ if ROOT not in sys.path:
 
 METRIC = "GB/s & % HBM peak for digest+dedup+census+compare; batched vs plain; p99 ms"
 NOMINAL_HBM_GBPS = 7900.0   # GB300 HBM3e nominal; fractions are also given against the measured copy peak
+MiB, GiB = 1 << 20, 1 << 30
+MOE_PAGE = 2 * MiB
+MOE_POOL = 64 * 24 * 20 * MiB
+MOE_PTRS = 64 * 24 * 8
+MOE_PAIR_ELEMS = 4096 * 7168
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)   # ~1.2 s timed: several clock samples inside it
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)   # ~1.5 s timed: several clock samples inside it
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="kc", choices=["kc", "reference"])
-    ap.add_argument("--variant", default="full", choices=["full", "152MB"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=6, help="0: skip the end-to-end measurement")
+    ap.add_argument("--moe-experts", type=int, default=64,
+                    help="experts per layer of the MoE pool (64: the 30 GiB pool; fewer: a smaller pool of the "
+                         "same shape, for profiling)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline time per thread setting")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-main", action="store_true",
+                    help="skip the headline MoE measurement (profiling runs of the other sections)")
+    ap.add_argument("--no-llama", action="store_true", help="skip the llama-shaped snapshot section")
+    ap.add_argument("--llama-steps", type=int, default=500)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
     ap.add_argument("--batched-jobs", type=int, default=4096)
     ap.add_argument("--no-served", action="store_true", help="skip the served-form section")
-    ap.add_argument("--no-moe", action="store_true", help="skip the 30 GiB MoE-pool section")
     ap.add_argument("--no-snapshot-io", action="store_true", help="skip the save/load-to-disk section")
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--served-rate", type=float, default=50.0)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -67,6 +88,23 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def moe_config(experts: int = 64) -> dict:
+    """The headline workload, identical in both arms."""
+    pool = experts * 24 * 20 * MiB
+    return {"workload": f"moe-pool-{experts}x24x20MiB-bf16 + int64 array of {experts * 24} expert base VAs",
+            "snapshot_bytes": pool + experts * 24 * 8, "regions": 2,
+            "pages": pool // MOE_PAGE + 1, "page_bytes": MOE_PAGE,
+            "compare": "bf16 [4096,7168] x 2 pairs (one identical, one with 0.1% perturbed)"}
+
+
+def host_cores() -> dict:
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except Exception:
+        usable = os.cpu_count() or 1
+    return {"nproc": usable, "cpu_count": os.cpu_count()}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -128,46 +166,43 @@ class ClockSampler:
                 "samples": len(inside)}
 
 
-# ----------------------------------------------------------------------------- workload
+# ----------------------------------------------------------------------------- one step
 
-def make_workload(seed: int, variant: str, device: str):
-    import torch
-    from paper_2605_03208_gb300 import workloads as W
-    layout = W.llama_layout(seed, variant=variant)
-    dev = [torch.empty(int(s), dtype=torch.uint8, device=device) for s in layout.sizes]
-    snap = W.llama_fill(layout, [t.data_ptr() for t in dev], seed)
-    for t, r in zip(dev, snap.regions):
-        t.copy_(torch.from_numpy(r), non_blocking=False)
-    pairs = W.llama_pairs(seed)
-    return snap, dev, pairs
+def algorithmic_bytes(N, U, C, P, pairs):
+    return {"scan": N + 9 * P, "dedup": 2 * U, "restore": U + N, "compare": C + 64 * pairs}
 
 
 class KcStep:
-    """Outputs and the call sequence of one step through the C ABI."""
+    """Outputs and the call sequence of one step through the C ABI.
 
-    def __init__(self, ctx, snap, dev, pairs, device):
+    regions: [(device tensor, kc dtype)]; pairs: [(got tensor, want tensor,
+    kc dtype)] (any element type; compared as their bytes' dtype)."""
+
+    def __init__(self, ctx, regions, page_bytes, win, pairs, device):
         import torch
         from paper_2605_03208_gb300 import kc
-        from paper_2605_03208_gb300 import workloads as W
-        self.kc, self.ctx, self.snap, self.dev = kc, ctx, snap, dev
-        self.S = snap.page_bytes
-        self.b = kc.bufs([(t.data_ptr(), t.numel(), dt, 0) for t, dt in zip(dev, snap.dtypes)])
+        self.kc, self.ctx = kc, ctx
+        self.tensors = [t for t, _ in regions]
+        self.sizes = [t.numel() * t.element_size() for t in self.tensors]
+        self.S = page_bytes
+        self.b = kc.bufs([(t.data_ptr(), n, dt, 0) for (t, dt), n in zip(regions, self.sizes)])
         self.P = kc.page_count(self.b, self.S)
-        self.win = W.default_window(snap.bases, snap.sizes)
+        self.win = win
         self.cap = 1 << 16
         mk = lambda n, dt=torch.uint8: torch.empty(n, dtype=dt, device=device)  # noqa: E731
         self.hash = mk(self.P, torch.int64)
         self.zero = mk(self.P)
-        self.pf = mk(len(dev) + 1, torch.int64)
+        self.pf = mk(len(regions) + 1, torch.int64)
         self.hits = mk(self.cap * 24)
         self.counts = torch.zeros(2, dtype=torch.int64, device=device)
         self.table = mk(self.P * 16)
         self.arena = mk(self.P * self.S)
         self.nblobs = torch.zeros(1, dtype=torch.int64, device=device)
-        self.g = [torch.from_numpy(p.got.view(np.uint8)).to(device) for p in pairs]
-        self.w = [torch.from_numpy(p.want.view(np.uint8)).to(device) for p in pairs]
-        self.gb = kc.bufs([(x.data_ptr(), x.numel(), p.dtype, 0) for x, p in zip(self.g, pairs)])
-        self.wb = kc.bufs([(x.data_ptr(), x.numel(), p.dtype, 0) for x, p in zip(self.w, pairs)])
+        self.g = [g for g, _, _ in pairs]
+        self.w = [w for _, w, _ in pairs]
+        nb = lambda x: x.numel() * x.element_size()  # noqa: E731
+        self.gb = kc.bufs([(g.data_ptr(), nb(g), dt, 0) for g, _, dt in pairs])
+        self.wb = kc.bufs([(w.data_ptr(), nb(w), dt, 0) for _, w, dt in pairs])
         self.cmp = mk(len(pairs) * 64)
         # the comparison does not depend on the snapshot operations: it runs on
         # a second stream (and context), overlapped with them, joined at the end
@@ -175,8 +210,9 @@ class KcStep:
         self.side = torch.cuda.Stream()
         self.fork = torch.cuda.Event()
         self.join = torch.cuda.Event()
-        self.N = sum(int(s) for s in snap.sizes)
-        self.C = sum(x.numel() for x in self.g)
+        self.N = sum(self.sizes)
+        self.C = sum(nb(g) + nb(w) for g, w in zip(self.g, self.w))
+        self.npairs = len(pairs)
 
     def run(self, stream, ev=None):
         """Enqueue one step.  ev: optional dict of (start, stop) torch events:
@@ -216,65 +252,144 @@ class KcStep:
     def unique_bytes(self):
         nb = int(self.nblobs.cpu().numpy().view(np.uint64)[0])
         tbl = self.table.cpu().numpy().view(self.kc.PAGE_DTYPE)
-        # bytes of the canonical pages (blob slots hold S bytes, the page may be shorter)
-        lens = []
-        seen = set()
-        sizes = self.snap.sizes
-        for row in tbl:
-            b = int(row["blob"])
-            if b >= 0xFFFFFFFE or b in seen:
-                continue
-            seen.add(b)
-            lens.append(min(self.S, int(sizes[int(row["alloc_id"])]) - int(row["va_offset"])))
-        return nb, int(sum(lens))
+        canon = np.unique(tbl["blob"][tbl["blob"] < 0xFFFFFFFE], return_index=True)[1]
+        U = 0
+        for p in canon.tolist():
+            a, off = int(tbl["alloc_id"][p]), int(tbl["va_offset"][p])
+            U += min(self.S, int(self.sizes[a]) - off)
+        return nb, U
+
+    def close(self):
+        self.ctx_cmp.close()
 
 
-# DRAM traffic of one digest_kernel<census> launch on this workload, from the
-# ncu capture summarised in profiles/digest_kernel_llama400.md, valid only for
-# the kernel sources it was taken on (sha1 of each file, first 8 hex digits)
-# or sources that compile to the same machine code (kc_device.cuh has since
-# lost unused helpers only; every kernel's cubin is byte-identical).
-DIGEST_TRAFFIC = {"bytes": 402_742_016 + 3_258_624,
-                  "shape": {"warps": 2, "stages": 2, "chunk": 1024, "ctas": 396, "lanes": 1},
-                  "sources": {"k_digest.cu": "29459998", "digest_task.cuh": "411ed35a",
-                              "kc_device.cuh": "b25ab658"}}
+def measure_step(step, stream, steps, warmup, sampler=None):
+    """Warm up, split the step per call (instrumented eager pass), then time
+    exactly `steps` graph replays of the step with CUDA events."""
+    import torch
+    kc = step.kc
+    for _ in range(max(warmup, 3)):
+        step.run(stream)
+    st = step.ctx.sync(stream)
+    if st != kc.OK:
+        raise RuntimeError(f"device status after warm-up: {kc.status_name(st)}")
+    nblobs, U = step.unique_bytes()
+    ab = algorithmic_bytes(step.N, U, step.C, step.P, step.npairs)
+    ops = ["scan", "dedup", "restore", "compare"]
+    k_ops = max(3, min(steps, 20))
+    tr = {op: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k_ops)] for op in ops + ["digest_kernel"]}
+    for op in tr:           # torch creates the cudaEvent_t on first record
+        for a, b in tr[op]:
+            a.record(stream)
+            b.record(stream)
+    l0 = kc.launch_count()
+    for i in range(k_ops):
+        step.run(stream, {op: tr[op][i] for op in tr})
+    torch.cuda.synchronize()
+    launches_per_step = (kc.launch_count() - l0) // k_ops
+    op_ms = {op: statistics.mean(a.elapsed_time(b) for a, b in tr[op]) for op in tr}
+    cs = torch.cuda.Stream()
+    cs.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cs):
+        step.run(cs)
+    with torch.cuda.stream(cs):
+        graph.replay()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    with torch.cuda.stream(cs):
+        e0.record(cs)
+        for _ in range(steps):
+            graph.replay()
+        e1.record(cs)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if sampler:
+        time.sleep(0.3)
+        sampler.stop()
+    st = step.ctx.sync(stream)
+    if st != kc.OK:
+        raise RuntimeError(f"device status after timed steps: {kc.status_name(st)}")
+    del graph
+    return dict(ms_total=e0.elapsed_time(e1), ab=ab, U=U, nblobs=nblobs, op_ms=op_ms,
+                launches_per_step=launches_per_step, t0=t0, t1=t1)
 
 
-def digest_traffic(shape):
-    """DRAM bytes per digest launch measured by ncu, or None once any of the
-    kernel's sources, or the launch shape, differs from the ones the capture
-    was taken on."""
+def compare_alone(step, stream, reps=20):
+    """The step's comparison timed on its own (CUDA events around back-to-back
+    calls on one stream)."""
+    import torch
+    step.ctx_cmp.compare(step.gb, step.wb, 0.0, 0.0, step.cmp, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step.ctx_cmp.compare(step.gb, step.wb, 0.0, 0.0, step.cmp, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def ops_report(ab, op_ms, peak):
+    return {op: {"ms": op_ms[op], "GB/s": ab[op] / (op_ms[op] / 1000) / 1e9,
+                 "frac": ab[op] / (op_ms[op] / 1000) / 1e9 / peak, "algorithmic_bytes": ab[op]}
+            for op in ("scan", "dedup", "restore", "compare")}
+
+
+# DRAM traffic of one digest_kernel<census> launch, measured by ncu on the
+# same pool recipe scaled down to 4 experts per layer (961 pages of 2 MiB:
+# the full pool is too large to capture with ncu's memory save/restore) and
+# scaled to a full launch by pages, since every page is read once.  Valid
+# only for the kernel sources it was taken on (sha1 of each file, first 8 hex
+# digits); None otherwise.
+DIGEST_TRAFFIC = {"read": 2_014_168_832, "write": 3_499_008, "pages": 961, "page_bytes": 2 * MiB,
+                  "sources": {"k_digest.cu": "201944d9", "digest_task.cuh": "79b7a29c",
+                              "kc_device.cuh": "0f4aa7a3"}}
+
+
+def digest_traffic(pages: int, page_bytes: int):
+    """DRAM bytes of one digest launch over `pages` pages of `page_bytes`,
+    from the capture above, or None when it does not apply."""
     import hashlib
-    if shape != DIGEST_TRAFFIC["shape"]:
+    if page_bytes != DIGEST_TRAFFIC["page_bytes"]:
         return None
     for f, want in DIGEST_TRAFFIC["sources"].items():
-        path = os.path.join(ROOT, "paper_2605_03208_gb300", "csrc", f)
         try:
-            with open(path, "rb") as fh:
+            with open(os.path.join(ROOT, "paper_2605_03208_gb300", "csrc", f), "rb") as fh:
                 if hashlib.sha1(fh.read()).hexdigest()[:8] != want:
                     return None
         except OSError:
             return None
-    return DIGEST_TRAFFIC["bytes"]
+    per_page = (DIGEST_TRAFFIC["read"] + DIGEST_TRAFFIC["write"]) / DIGEST_TRAFFIC["pages"]
+    return int(round(per_page * pages))
 
 
-def algorithmic_bytes(N, U, C, P, pairs):
-    return {"scan": N + 9 * P, "dedup": 2 * U, "restore": U + N, "compare": C + 64 * pairs}
+def roofline(ctx, step, ab, op_ms, peak, peak_kind, traffic):
+    achieved = ab["scan"] / (op_ms["digest_kernel"] / 1000) / 1e9
+    shape = ctx.digest_shape(step.S, step.P)
+    return {"bound": "hbm", "kernel": "digest_kernel<census> (kc_scan)", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBPS, "traffic": traffic, "shape": shape,
+            "algorithmic_bytes": ab["scan"], "kernel_ms": op_ms["digest_kernel"],
+            "algorithmic_bytes_rule": "N + 9 B/page (snapshot read once, hash + zero flag written)"}
 
 
 # ----------------------------------------------------------------------------- oracle leg
 
-def oracle_step(snap, pairs, sample_regions=None):
-    """One pass of the oracle over (a sample of) the workload; returns bytes-defined units."""
+def oracle_step(snap, pairs):
+    """One pass of the oracle over a host snapshot and its pairs; returns the
+    step's algorithmic bytes (the metric's unit) and the snapshot bytes."""
     import oracle
     from paper_2605_03208_gb300 import workloads as W
-    idx = list(range(len(snap.sizes))) if sample_regions is None else sample_regions
-    regions = [snap.regions[i] for i in idx]
-    bases = [snap.bases[i] for i in idx]
-    S = snap.page_bytes
-    win = W.default_window(snap.bases, snap.sizes)
+    regions, bases, S = snap.regions, snap.bases, snap.page_bytes
+    win = W.default_window(bases, snap.sizes)
     h, z, pf = oracle.digest(regions, S)
-    oracle.census(regions, bases, *win)
+    oracle.census(regions, bases, *win, cap=1 << 16)
     t = oracle.dedup(regions, S, h, z)
     arena = oracle.pack(regions, S, t)
     targets = [np.empty_like(r) for r in regions]
@@ -292,41 +407,70 @@ def oracle_step(snap, pairs, sample_regions=None):
     return sum(ab.values()), N
 
 
+def oracle_throughput(snap, pairs, threads: int, seconds: float) -> dict:
+    """Run the oracle, as it stands, on `threads` host threads at once (each
+    its own pass over the same read-only sample) for about `seconds`;
+    returns the whole throughput in the metric's unit."""
+    oracle_step(snap, pairs)                   # builds and loads the library, warms the caches
+    stop = time.perf_counter() + seconds
+    done = [0] * threads
+
+    def worker(i):
+        n = 0
+        while time.perf_counter() < stop or n == 0:
+            b, _ = oracle_step(snap, pairs)
+            done[i] += b
+            n += 1
+        return n
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        passes = sum(ex.map(worker, range(threads)))
+    dt = time.perf_counter() - t0
+    return {"value": sum(done) / dt / 1e9, "passes": passes, "seconds": dt}
+
+
+def cpu_baseline(seed: int, seconds: float) -> dict:
+    """The oracle on the host cores: single thread, and one thread per usable
+    core, over a host sample of the MoE workload (its recipe, 32 pages)."""
+    from paper_2605_03208_gb300 import workloads as W
+    snap, pairs = W.moe_host_sample(seed, pages=32)
+    cores = host_cores()
+    one = oracle_throughput(snap, pairs, 1, seconds)
+    allc = oracle_throughput(snap, pairs, cores["nproc"], seconds)
+    sample = (f"MoE recipe on the host: 32 pages of 2 MiB bf16 (64 MiB, 2% duplicate pages) + the 1536-entry "
+              f"expert pointer array + 2 bf16 pairs of 256 x 7168; each pass digest, census, dedup, pack, "
+              f"restore, compare; GB/s of the step's algorithmic bytes")
+    return {"value": allc["value"], "unit": "GB/s", "cores": cores["nproc"], "kind": "oracle",
+            "sample": sample, "single_thread": {"value": one["value"], "cores": 1, "passes": one["passes"]},
+            "all_cores": {"value": allc["value"], "cores": cores["nproc"], "passes": allc["passes"],
+                          "how": "one thread per usable core, each running the unmodified oracle on the "
+                                 "same read-only sample (ctypes releases the GIL)"},
+            "host": cores}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from paper_2605_03208_gb300 import workloads as W
-    layout = W.llama_layout(args.seed, variant=args.variant)
-    snap = W.llama_fill(layout, W.fake_bases(layout.sizes, args.seed), args.seed)
-    pairs = W.llama_pairs(args.seed)
-    # size the per-step sample so the whole run ends within ~3 minutes
-    t0 = time.perf_counter()
-    oracle_step(snap, pairs, sample_regions=list(range(0, len(snap.sizes), 8)))
-    t_probe = (time.perf_counter() - t0) * 8
-    budget = 150.0 / max(args.steps + args.warmup, 1)
-    frac = min(1.0, budget / max(t_probe, 1e-6))
-    stride = max(1, int(round(1.0 / frac)))
-    sample = list(range(0, len(snap.sizes), stride))
+    snap, pairs = W.moe_host_sample(args.seed, pages=32)
     for _ in range(args.warmup):
-        oracle_step(snap, pairs, sample)
-    times, abytes = [], 0
+        oracle_step(snap, pairs)
+    times, abytes, Nsamp = [], 0, 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        abytes, Nsamp = oracle_step(snap, pairs, sample)
+        abytes, Nsamp = oracle_step(snap, pairs)
         times.append(time.perf_counter() - t0)
-    ms = 1000 * statistics.mean(times)
-    value = abytes / (ms / 1000) / 1e9
+    ms = 1000 * statistics.mean(times) if times else 0.0
+    value = abytes / (ms / 1000) / 1e9 if ms else 0.0
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": snap.name, "regions": len(snap.sizes),
-                       "snapshot_bytes": snap.total_bytes, "page_bytes": snap.page_bytes,
-                       "compare": "fp32 [8,32000] x 2 pairs"},
+            "data": "synthetic", "impl": "reference", "config": moe_config(),
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"every {stride}th region ({len(sample)} of "
-                                       f"{len(snap.sizes)}, {Nsamp} bytes) + both compare pairs"},
+                             "sample": f"each step: a host sample of the MoE workload ({Nsamp} snapshot bytes: "
+                                       "32 pages of 2 MiB + the pointer array, 2 bf16 pairs of 256 x 7168)"},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -353,10 +497,84 @@ def whole_job_gbps(world: int, bytes_per_replica_step: float, ms_per_step: float
 
 # ----------------------------------------------------------------------------- GPU leg
 
+def make_moe(seed, device, experts=64):
+    import torch
+    from paper_2605_03208_gb300 import kc
+    from paper_2605_03208_gb300 import workloads as W
+    snap, (pool, ptrs) = W.moe_snapshot(seed, experts=experts, device=device)
+    pairs = [(g.view(torch.uint8), w.view(torch.uint8), kc.BF16) for g, w, _ in W.moe_pairs(seed, device=device)]
+    return snap, pool, ptrs, pairs
+
+
+def run_e2e(step, ctx, pool, ptrs, device, k):
+    """The same step through the C ABI from host buffers: every step
+    ingests the snapshot from a pinned, page-slotted host image (kc_restore
+    with the identity page table reads it over the host link and writes
+    every page to its region's VA offset), copies the comparison inputs in,
+    runs the step and reads every output back.  Returns (ms per step, h2d,
+    d2h bytes per step)."""
+    import torch
+    from paper_2605_03208_gb300 import kc
+    S, P = step.S, step.P
+    pfirst = np.concatenate([[0], np.cumsum([-(-int(x) // S) for x in step.sizes])]).astype(np.int64)
+    img = torch.empty(P * S, dtype=torch.uint8, pin_memory=True)
+    for i, t in enumerate(step.tensors):
+        o = int(pfirst[i]) * S
+        img[o:o + step.sizes[i]].copy_(t.view(torch.uint8).view(-1))
+    ident = np.zeros(P, dtype=kc.PAGE_DTYPE)
+    for i in range(len(step.sizes)):
+        pages = np.arange(int(pfirst[i]), int(pfirst[i + 1]))
+        ident["va_offset"][pages] = (pages - pfirst[i]) * S
+        ident["alloc_id"][pages] = i
+        ident["blob"][pages] = pages
+    ident_d = torch.from_numpy(ident.view(np.uint8).copy()).to(device)
+    host_g = [x.cpu().pin_memory() for x in step.g]
+    host_w = [x.cpu().pin_memory() for x in step.w]
+    outs = [step.hash, step.zero, step.counts, step.table, step.nblobs, step.cmp]
+    host_out = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+    s = torch.cuda.Stream()
+
+    def lane_step():
+        ctx.restore(step.b, S, ident_d, P, img, P * S, s)
+        for d, h in zip(step.g + step.w, host_g + host_w):
+            d.copy_(h, non_blocking=True)
+        step.run(s)
+        for h, o in zip(host_out, outs):
+            h.copy_(o, non_blocking=True)
+
+    torch.cuda.synchronize()
+    ref_hash = step.hash.cpu().clone()
+    ref_counts = step.counts.cpu().clone()
+    for t in step.tensors:            # the ingest path must rebuild the snapshot from the host image
+        t.zero_()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        lane_step()
+    torch.cuda.synchronize()
+    if not (torch.equal(host_out[0], ref_hash) and torch.equal(host_out[2], ref_counts)):
+        raise RuntimeError("end-to-end ingest did not reproduce the snapshot (digests differ)")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        lane_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        for _ in range(k):
+            g.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    h2d = sum(step.sizes) + sum(x.numel() for x in host_g + host_w)
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    del g, img
+    return e0.elapsed_time(e1) / k, h2d, d2h
+
+
 def run_kc(args):
     import torch
     import torch.distributed as dist
     from paper_2605_03208_gb300 import kc
+    from paper_2605_03208_gb300 import workloads as W
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -366,9 +584,21 @@ def run_kc(args):
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
     kc.load()
+    peak, peak_kind = peaks()
     ctx = kc.Context(local)
-    snap, dev, pairs = make_workload(args.seed + rank, args.variant, device)
-    step = KcStep(ctx, snap, dev, pairs, device)
+    if args.no_main:
+        line = {"metric": METRIC, "note": "headline measurement skipped (--no-main)"}
+        if not args.no_llama:
+            line["llama"] = run_llama_section(args, ctx, device, peak, peak_kind)
+        if rank == 0:
+            print(json.dumps(line))
+        ctx.close()
+        return 0
+    t_gen = time.time()
+    snap, pool, ptrs, pairs = make_moe(args.seed + rank, device, args.moe_experts)
+    t_gen = time.time() - t_gen
+    step = KcStep(ctx, [(pool, kc.BF16), (ptrs, kc.RAW)], snap.page_bytes,
+                  W.default_window(snap.bases, snap.sizes), pairs, device)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -376,210 +606,108 @@ def run_kc(args):
         if world > 1:
             dist.barrier()
 
-    # warm-up (also sizes the context's scratch)
-    for _ in range(max(args.warmup, 3)):
-        step.run(stream)
-    st = ctx.sync(stream)
-    if st != kc.OK:
-        raise RuntimeError(f"device status after warm-up: {kc.status_name(st)}")
-    nblobs, U = step.unique_bytes()
-    ab = algorithmic_bytes(step.N, U, step.C, step.P, len(pairs))
-    step_bytes = sum(ab.values())
-
-    # ---- per-operation split and the roofline kernel: an instrumented pass
-    # (events around every call, and around the digest kernel by the library)
-    ops = ["scan", "dedup", "restore", "compare"]
-    k_ops = max(3, min(args.steps, 50))
-    tr = {op: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(k_ops)] for op in ops + ["digest_kernel"]}
-    for op in tr:           # torch creates the cudaEvent_t on first record
-        for a, b in tr[op]:
-            a.record(stream)
-            b.record(stream)
-    l0 = kc.launch_count()
-    for i in range(k_ops):
-        step.run(stream, {op: tr[op][i] for op in tr})
-    torch.cuda.synchronize()
-    launches_per_step = (kc.launch_count() - l0) // k_ops
-    op_ms = {op: statistics.mean(a.elapsed_time(b) for a, b in tr[op]) for op in tr}
-
-    # ---- timed region: exactly K steps, replays of the step captured once as
-    # a CUDA graph (the same kernels; the host's launch work is taken out), on
-    # the capture stream; device time with CUDA events, no events inside
-    cs = torch.cuda.Stream()
-    cs.wait_stream(stream)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=cs):
-        step.run(cs)
-    with torch.cuda.stream(cs):
-        graph.replay()
-    torch.cuda.synchronize()
+    barrier()
     sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
+    m = measure_step(step, stream, args.steps, args.warmup, sampler)
+    ms = max_over_ranks(m["ms_total"], world, device) / args.steps
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_wall0 = time.time()
-    with torch.cuda.stream(cs):
-        e0.record(cs)
-        for i in range(args.steps):
-            graph.replay()
-        e1.record(cs)
-    barrier()
-    t_wall1 = time.time()
-    launches = launches_per_step * args.steps
-    ms_total = max_over_ranks(e0.elapsed_time(e1), world, device)
-    ms = ms_total / args.steps
-    time.sleep(0.3)
-    sampler.stop()
-    st = ctx.sync(stream)
-    if st != kc.OK:
-        raise RuntimeError(f"device status after timed steps: {kc.status_name(st)}")
-    del graph
-
-    # ---- end to end: pinned host inputs brought in, results read back, every step.
-    # A snapshot is one pinned host image with each page in an S-byte slot (a
-    # packed snapshot's layout); kc_restore with the identity page table reads
-    # it over the host link and writes every page to its region's VA offset
-    # (one launch instead of one copy per region; on this machine as fast as a
-    # copy-engine copy of the image, and it overlaps the other lane's work
-    # better than one).  Two lanes --
-    # two region sets holding the same workload at their own VAs, each with
-    # its own stream and contexts -- alternate, so one lane's ingest over the
-    # host link overlaps the other lane's device work.
-    def make_lane(step_, snap_, dev_, ctx_, s_):
-        S_, P_ = step_.S, step_.P
-        pfirst = np.concatenate([[0], np.cumsum([-(-int(x) // S_) for x in snap_.sizes])]).astype(np.int64)
-        img = torch.zeros(P_ * S_, dtype=torch.uint8, pin_memory=True)
-        ident = np.zeros(P_, dtype=kc.PAGE_DTYPE)
-        for i, r in enumerate(snap_.regions):
-            o = int(pfirst[i]) * S_
-            img[o:o + r.size] = torch.from_numpy(r)
-            pages = np.arange(int(pfirst[i]), int(pfirst[i + 1]))
-            ident["va_offset"][pages] = (pages - pfirst[i]) * S_
-            ident["alloc_id"][pages] = i
-            ident["blob"][pages] = pages
-        lane = dict(step=step_, snap=snap_, dev=dev_, ctx=ctx_, s=s_, img=img,
-                    ident=torch.from_numpy(ident.view(np.uint8).copy()).to(device),
-                    host_g=[x.cpu().pin_memory() for x in step_.g], host_w=[x.cpu().pin_memory() for x in step_.w],
-                    outs=[step_.hash, step_.zero, step_.counts, step_.table, step_.nblobs, step_.cmp])
-        lane["host_out"] = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in lane["outs"]]
-        return lane
-
-    def lane_step(L):
-        st_ = L["step"]
-        L["ctx"].restore(st_.b, st_.S, L["ident"], st_.P, L["img"], st_.P * st_.S, L["s"])
-        for d, h in zip(st_.g + st_.w, L["host_g"] + L["host_w"]):
-            d.copy_(h, non_blocking=True)
-        st_.run(L["s"])
-        for h, o in zip(L["host_out"], L["outs"]):
-            h.copy_(o, non_blocking=True)
-
-    ctx_b = kc.Context(local)
-    snap_b, dev_b, pairs_b = make_workload(args.seed + rank, args.variant, device)
-    step_b = KcStep(ctx_b, snap_b, dev_b, pairs_b, device)
-    lanes = [make_lane(step, snap, dev, ctx, torch.cuda.Stream()),
-             make_lane(step_b, snap_b, dev_b, ctx_b, torch.cuda.Stream())]
-    h2d = lanes[0]["img"].numel() + sum(x.numel() for x in lanes[0]["host_g"] + lanes[0]["host_w"])
-    d2h = sum(o.numel() * o.element_size() for o in lanes[0]["outs"])
-    k_e2e = max(4, min(args.steps, 50)) // 2 * 2
-    for L in lanes:        # the ingest path must reproduce each lane's snapshot exactly
-        for t in L["dev"]:
-            t.zero_()
-        L["s"].wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(L["s"]):
-            lane_step(L)   # (also warms the lane's table caches)
-    torch.cuda.synchronize()
-    for L in lanes:
-        for t, r in zip(L["dev"], L["snap"].regions):
-            if not np.array_equal(t.cpu().numpy(), r):
-                raise RuntimeError("end-to-end ingest did not reproduce the snapshot")
-    for L in lanes:        # each lane's whole iteration (ingest, copies, step, read-back) as a graph
-        L["graph"] = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(L["graph"], stream=L["s"]):
-            lane_step(L)
-    torch.cuda.synchronize()
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for L in lanes:
-        L["s"].wait_event(f0)
-    for i in range(k_e2e):
-        L = lanes[i % 2]
-        with torch.cuda.stream(L["s"]):
-            L["graph"].replay()
-    for L in lanes:
-        stream.wait_stream(L["s"])
-    f1.record(stream)
-    barrier()
-    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / k_e2e, world, device)
-
-    peak, peak_kind = peaks()
+    ab = m["ab"]
+    step_bytes = sum(ab.values())
+    cnt = step.counts.cpu().numpy().view(np.uint64)
+    cmp_ms = compare_alone(step, stream)
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e_ms, h2d, d2h = run_e2e(step, ctx, pool, ptrs, device, args.e2e_steps)
+        e2e_ms = max_over_ranks(e2e_ms, world, device)
+        e2e = {"value": whole_job_gbps(world, step_bytes, e2e_ms), "unit": "GB/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ingest": "kc_restore with the identity page table reads the page-slotted snapshot image "
+                         "from pinned host memory every step; compare inputs copied in; every output read "
+                         "back; the iteration replayed as a CUDA graph"}
     value = whole_job_gbps(world, step_bytes, ms)
-    scan_bytes = ab["scan"]
-    achieved = scan_bytes / (op_ms["digest_kernel"] / 1000) / 1e9
+    ops = ops_report(ab, m["op_ms"], peak)
+    ops["compare"] = {"ms": cmp_ms, "GB/s": ab["compare"] / (cmp_ms / 1000) / 1e9,
+                      "frac": ab["compare"] / (cmp_ms / 1000) / 1e9 / peak, "algorithmic_bytes": ab["compare"],
+                      "timing": "alone (back-to-back calls); in the step it overlaps the other calls on a "
+                                "second stream"}
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": snap.name, "regions": len(snap.sizes), "snapshot_bytes": step.N,
-                   "pages": step.P, "page_bytes": step.S, "unique_bytes": U, "blobs": nblobs,
-                   "compare": "fp32 [8,32000] x 2 pairs", "parallelism": f"replicas{world}",
-                   "l2": "inputs (0.39 GiB) larger than L2; no flush",
-                   "step": "scan(digest+census) + dedup(+pack) + restore, and compare on a second "
-                           "stream overlapped with them; timed as CUDA graph replays of the step"},
+        "config": moe_config(args.moe_experts),
+        "parallelism": f"replicas{world}",
+        "workload_detail": {"unique_bytes": m["U"], "blobs": m["nblobs"], "census_inside": int(cnt[0]),
+                            "census_outside": int(cnt[1]), "gen_s": round(t_gen, 2),
+                            "l2": "inputs (30 GiB) larger than the 129 MB L2; no flush",
+                            "step": "scan(digest+census) + dedup(+pack) + restore, and compare on a second "
+                                    "stream overlapped with them; timed as CUDA graph replays of the step"},
         "hbm_frac": value / world / peak,
         "hbm_frac_of_nominal": value / world / NOMINAL_HBM_GBPS,
-        "roofline": {"bound": "hbm", "kernel": "digest_kernel<census> (kc_scan)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "frac_of_nominal": achieved / NOMINAL_HBM_GBPS,
-                     "traffic": digest_traffic(ctx.digest_shape(step.S, step.P)),
-                     "shape": ctx.digest_shape(step.S, step.P), "algorithmic_bytes": scan_bytes,
-                     "kernel_ms": op_ms["digest_kernel"]},
-        "ops": {op: {"ms": op_ms[op], "GB/s": ab[op] / (op_ms[op] / 1000) / 1e9,
-                     "frac": ab[op] / (op_ms[op] / 1000) / 1e9 / peak,
-                     "algorithmic_bytes": ab[op]} for op in ops},
-        "ops_timing": "instrumented eager pass: CUDA events around each whole call (all of its "
-                      "kernels); the roofline kernel is timed by events the library records around it "
-                      "alone; the timed region replays the step as a CUDA graph (no events inside)",
-        "launches_per_step": launches_per_step,
-        "e2e": {"value": whole_job_gbps(world, step_bytes, e2e_ms), "unit": "GB/s",
-                "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ingest": "kc_restore with the identity page table reads the page-slotted snapshot image "
-                          "from pinned host memory; compare inputs copied in; outputs read back every step; "
-                          "two lanes (region sets at their own VAs, own streams) alternate so that one "
-                          "lane's ingest overlaps the other's device work; each lane's iteration replayed "
-                          "as a CUDA graph"},
-        "gpu_launches": launches,
-        "clocks": sampler.summary(t_wall0, t_wall1),
+        "roofline": roofline(ctx, step, ab, m["op_ms"], peak, peak_kind, digest_traffic(step.P, step.S)),
+        "ops": ops,
+        "ops_timing": "instrumented eager pass: CUDA events around each whole call (all of its kernels); the "
+                      "roofline kernel is timed by events the library records around it alone; the timed "
+                      "region replays the step as a CUDA graph (no events inside)",
+        "launches_per_step": m["launches_per_step"],
+        "e2e": e2e,
+        "gpu_launches": m["launches_per_step"] * args.steps,
+        "clocks": sampler.summary(m["t0"], m["t1"]),
     }
-    if not args.no_snapshot_io:
-        line["snapshot_io"] = run_snapshot_io_section(ctx, step, snap, dev)
-    if not args.no_moe:
-        line["moe"] = run_moe_section(args, device, peak)
+    step.close()
+    del step, pool, ptrs, pairs
+    torch.cuda.empty_cache()
+    if not args.no_llama:
+        line["llama"] = run_llama_section(args, ctx, device, peak, peak_kind)
     if not args.no_batched:
         line["batched"] = run_batched_section(args, device, peak)
     if not args.no_served:
         line["served"] = run_served_section(args, device)
     if rank == 0 and not args.no_cpu_baseline:
-        t0 = time.perf_counter()
-        sample = list(range(len(snap.sizes)))
-        ob, _ = oracle_step(snap, pairs, sample)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": ob / dt / 1e9, "unit": "GB/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": "one full step of the same workload (all 400 regions,"
-                                          " both pairs), single thread"}
+        line["cpu_baseline"] = cpu_baseline(args.seed, args.cpu_seconds)
     if world > 1:
         dist.barrier()
     if rank == 0:
         print(json.dumps(line))
-    ctx_b.close()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_llama_section(args, ctx, device, peak, peak_kind):
+    """The llama.cpp-shaped snapshot (400 regions, 64 KiB pages, fp32 logits
+    pairs), full and "152MB" variants: the same step, timed the same way."""
+    import torch
+    from paper_2605_03208_gb300 import kc
+    from paper_2605_03208_gb300 import workloads as W
+    out = {}
+    stream = torch.cuda.current_stream()
+    for variant in ("full", "152MB"):
+        layout = W.llama_layout(args.seed, variant=variant)
+        dev = [torch.empty(int(s), dtype=torch.uint8, device=device) for s in layout.sizes]
+        snap = W.llama_fill(layout, [t.data_ptr() for t in dev], args.seed)
+        for t, r in zip(dev, snap.regions):
+            t.copy_(torch.from_numpy(r), non_blocking=False)
+        pairs = [(torch.from_numpy(p.got.view(np.uint8)).to(device), torch.from_numpy(p.want.view(np.uint8)).to(device),
+                  p.dtype) for p in W.llama_pairs(args.seed)]
+        step = KcStep(ctx, list(zip(dev, snap.dtypes)), snap.page_bytes, W.default_window(snap.bases, snap.sizes),
+                      pairs, device)
+        m = measure_step(step, stream, args.llama_steps, args.warmup)
+        ms = m["ms_total"] / args.llama_steps
+        value = sum(m["ab"].values()) / (ms / 1000) / 1e9
+        sec = {"workload": snap.name, "regions": len(snap.sizes), "snapshot_bytes": step.N, "pages": step.P,
+               "page_bytes": step.S, "unique_bytes": m["U"], "blobs": m["nblobs"],
+               "compare": "fp32 [8,32000] x 2 pairs", "value": value, "unit": "GB/s", "ms_per_step": ms,
+               "steps": args.llama_steps, "hbm_frac": value / peak,
+               "roofline": roofline(ctx, step, m["ab"], m["op_ms"], peak, peak_kind, None),
+               "ops": ops_report(m["ab"], m["op_ms"], peak), "launches_per_step": m["launches_per_step"]}
+        if variant == "full" and not args.no_snapshot_io:
+            sec["snapshot_io"] = run_snapshot_io_section(ctx, step, snap, dev)
+        out[variant] = sec
+        step.close()
+        del step, dev, pairs
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batched_section(args, device, peak):
@@ -705,83 +833,6 @@ def run_snapshot_io_section(ctx, step, snap, dev):
         shutil.rmtree(d, ignore_errors=True)
 
 
-def run_moe_section(args, device, peak):
-    """The 30 GiB MoE weight pool (64 experts x 24 layers x 20 MiB of bf16,
-    2% duplicate pages, an int64 array of the 1536 expert pointers), 2 MiB
-    pages: each operation timed on its own with CUDA events (inputs far
-    larger than L2), plus the bf16 [4096, 7168] comparison pairs."""
-    import torch
-    from paper_2605_03208_gb300 import kc
-    from paper_2605_03208_gb300 import workloads as W
-
-    free, _ = torch.cuda.mem_get_info()
-    if free < 75 * W.GiB:
-        return {"skipped": f"needs ~75 GiB free device memory, {free / W.GiB:.0f} GiB free"}
-    t0 = time.time()
-    snap, dev = W.moe_snapshot(args.seed, device=device)
-    pairs = W.moe_pairs(args.seed, device=device)
-    t_gen = time.time() - t0
-    pool, ptrs = dev
-    S = snap.page_bytes
-    ctx = kc.Context(torch.cuda.current_device())
-    b = kc.bufs([(pool.data_ptr(), pool.numel(), kc.BF16, 0), (ptrs.data_ptr(), ptrs.numel() * 8, kc.RAW, 0)])
-    P = kc.page_count(b, S)
-    N = pool.numel() + ptrs.numel() * 8
-    win = W.default_window(snap.bases, snap.sizes)
-    mk = lambda n, dt=torch.uint8: torch.empty(n, dtype=dt, device=device)  # noqa: E731
-    h, z, pf = mk(P, torch.int64), mk(P), mk(3, torch.int64)
-    cap = 1 << 16
-    hits, counts = mk(cap * 24), torch.zeros(2, dtype=torch.int64, device=device)
-    table, nb = mk(P * 16), torch.zeros(1, dtype=torch.int64, device=device)
-    arena = mk(P * S)
-    gb = kc.bufs([(g.data_ptr(), g.numel() * 2, kc.BF16, 0) for g, _, _ in pairs])
-    wb = kc.bufs([(w.data_ptr(), w.numel() * 2, kc.BF16, 0) for _, w, _ in pairs])
-    rec = mk(len(pairs) * 64)
-    C = sum(g.numel() * 2 * 2 for g, _, _ in pairs)
-    st = torch.cuda.current_stream()
-    ops = {
-        "scan": lambda: ctx.scan(b, S, h, z, pf, win[0], win[1], hits, cap, counts, st),
-        "dedup": lambda: ctx.dedup(b, S, h, z, table, arena, P * S, nb, st),
-        "restore": lambda: ctx.restore(b, S, table, P, arena, P * S, st),
-        "compare": lambda: ctx.compare(gb, wb, 0.0, 0.0, rec, st),
-    }
-    reps = {"scan": 5, "dedup": 3, "restore": 3, "compare": 20}
-    out = {}
-    for op in ("scan", "dedup", "restore", "compare"):
-        ops[op]()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(reps[op]):
-            ops[op]()
-        e1.record(st)
-        e1.synchronize()
-        out[op] = e0.elapsed_time(e1) / reps[op]
-    if ctx.sync(st) != kc.OK:
-        raise RuntimeError("MoE section: device status not OK")
-    cnt = counts.cpu().numpy().view(np.uint64)
-    n_blobs = int(nb.cpu().numpy().view(np.uint64)[0])
-    tbl = table.cpu().numpy().view(kc.PAGE_DTYPE)
-    canon_pages = np.unique(tbl["blob"][tbl["blob"] < 0xFFFFFFFE], return_index=True)[1]
-    U = 0
-    for p in canon_pages.tolist():
-        a, off = int(tbl["alloc_id"][p]), int(tbl["va_offset"][p])
-        U += min(S, int(snap.sizes[a]) - off)
-    ab = {"scan": N + 9 * P, "dedup": 2 * U, "restore": U + N, "compare": C + 64 * len(pairs)}
-    res = {op: {"ms": out[op], "GB/s": ab[op] / (out[op] / 1000) / 1e9,
-                "frac": ab[op] / (out[op] / 1000) / 1e9 / peak, "algorithmic_bytes": ab[op]} for op in out}
-    summary = {
-        "workload": snap.name + ", int64 pointer array of 1536 expert bases, 2 MiB pages; bf16 [4096,7168] x 2 pairs",
-        "snapshot_bytes": N, "pages": P, "unique_bytes": U, "blobs": n_blobs,
-        "census_inside": int(cnt[0]), "census_outside": int(cnt[1]), "gen_s": round(t_gen, 2),
-        "ops": res, "timing": "CUDA events around each call, repeated back to back; inputs 30 GiB > L2",
-    }
-    ctx.close()
-    del pool, ptrs, dev, arena, pairs
-    torch.cuda.empty_cache()
-    return summary
-
-
 def run_served_section(args, device):
     """Served form: 64 golden buffers resident (log-uniform 1 MiB - 2 GiB,
     mixed dtypes), a Poisson stream of digest / compare requests at
@@ -846,8 +897,8 @@ def run_served_section(args, device):
     return out
 
 
-def main():
-    args = parse()
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
     return run_kc(args)

@@ -443,8 +443,10 @@ DigestShape pick_digest_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
         if (per_sm < 1) per_sm = 1;
         if (per_sm > 8) per_sm = 8;
         s.warps = (int)per_sm;
-        static const int pref[][2] = {{2048, 2}, {1024, 3}, {1024, 4}, {512, 4}, {1024, 2},
-                                      {512, 3},  {512, 2},  {256, 4},  {256, 3}, {256, 2}};
+        // few hash warps per SM: each one's chains run fastest, so it needs
+        // more bytes in flight; deeper rings first while they fit
+        static const int pref[][2] = {{2048, 6}, {2048, 4}, {2048, 3}, {2048, 2}, {1024, 3}, {1024, 4},
+                                      {512, 4},  {1024, 2}, {512, 3},  {512, 2},  {256, 4},  {256, 3}, {256, 2}};
         s.chunk = 256;
         s.stages = 2;
         for (auto &pc : pref) {

@@ -376,6 +376,46 @@ def moe_snapshot(seed: int = 0, experts: int = MOE_EXPERTS, layers: int = MOE_LA
     return snap, [pool, ptrs]
 
 
+def moe_host_sample(seed: int = 0, pages: int = 32, page_bytes: int = 2 * MiB, dup_frac: float = 0.02,
+                    pair_rows: int = 256, cols: int = 7168) -> tuple:
+    """A host-side sample of the MoE workload with the pool's recipe, for
+    CPU-side timing where the whole 30 GiB pool is not wanted: `pages` pages
+    of bf16 ~ N(0, 0.02) with no exact zeros (torch's CPU generator), dup_frac
+    of them overwritten with copies of other pages of the sample, the int64
+    array of the 1536 expert base VAs (experts of 20 MiB from a fake pool
+    base), and the two bf16 comparison pairs cut to `pair_rows` rows (one
+    identical, one with 0.1% of elements one ulp away in the bit pattern).
+    Returns (Snapshot with host regions, [Pair, Pair])."""
+    import torch
+    g = torch.Generator()
+    g.manual_seed(seed + 909)
+    n = pages * page_bytes // 2
+    x = (torch.randn(n, generator=g) * 0.02).to(torch.bfloat16)
+    tiny = torch.tensor(2.0 ** -120, dtype=torch.bfloat16)
+    x = torch.where(x == 0, tiny, x)
+    pool = x.view(torch.uint8).numpy().copy()
+    rng = np.random.default_rng(seed + 910)
+    ndup = int(round(pages * dup_frac))
+    if ndup:
+        perm = rng.permutation(pages)
+        pv = pool.reshape(pages, page_bytes)
+        for d, s_ in zip(np.sort(perm[:ndup]).tolist(), rng.choice(perm[ndup:], ndup).tolist()):
+            pv[d] = pv[s_]
+    n_exp = MOE_EXPERTS * MOE_LAYERS
+    bases = fake_bases([pages * page_bytes, n_exp * 8], seed)
+    vals = np.array([bases[0] + (e * MOE_EXPERT_BYTES) % (pages * page_bytes) for e in range(n_exp)], dtype=np.uint64)
+    ptrs = vals.view(np.uint8).copy()
+    snap = Snapshot(f"moe-pool-sample-{pages}x{page_bytes // MiB}MiB", page_bytes, [pool.size, ptrs.size],
+                    bases, [pool, ptrs], [DT_BF16, DT_RAW])
+    m = pair_rows * cols
+    want = (torch.randn(m, generator=g)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16).copy()
+    want2 = (torch.randn(m, generator=g)).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16).copy()
+    idx = np.sort(rng.choice(m, m // 1000, replace=False))
+    got = want.copy()
+    got[idx] = want[idx] ^ np.uint16(1)          # one ulp of the bit pattern
+    return snap, [Pair(want2.copy(), want2, DT_BF16), Pair(got, want, DT_BF16, dict(perturbed=idx))]
+
+
 def moe_pairs(seed: int = 0, rows: int = 4096, cols: int = 7168, device: str = "cuda"):
     """bf16 [rows, cols] ~ N(0, 1): one identical pair and one pair with 0.1% of
     elements times (1 +- 1e-2) (a step of one ulp where that rounds away).
