@@ -330,6 +330,41 @@ KC_API kc_status kc_restore(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t p
 KC_API kc_status kc_compare(kc_ctx *ctx, const kc_buf *got, const kc_buf *want, int npairs,
                      double atol, double rtol, kc_cmp_result *d_out, void *stream);
 
+/* ---- exact-VA reservation (replay in a fresh process) ---------------------
+ * A snapshot's embedded device pointers are valid only at the VAs it was
+ * captured at, so the paper's replay reserves every captured region's
+ * address before copying the data back (Section "VA-Faithful HSA Replay",
+ * stages 4-5; Section "Memory Capture", paragraph "Handling embedded device
+ * pointers via address-space closure").  kc_va_reserve does that for a
+ * process that did not capture the snapshot: every region of `regions`
+ * (base_va, bytes; dtype and flags ignored) on CUDA device `device` gets
+ * physical device memory mapped at exactly [base_va, base_va + bytes)
+ * rounded out to the device's allocation granularity (regions sharing a
+ * granule share the mapping), readable and writable by the device.
+ * kc_restore with the same descriptors then writes every page at its
+ * captured VA.  The CUDA driver treats a requested address as a hint it may
+ * not honour; it places a large reservation at the lowest free address of
+ * its large-reservation zone, where VMM-based allocators (PyTorch with
+ * expandable segments) also place their memory.  So the call makes one
+ * covering VA reservation (at least 4 GiB, no memory) and keeps it only if
+ * it spans every captured range -- which holds when the snapshot was
+ * allocated that way and the calling process has not yet used that zone --
+ * and maps memory at the captured ranges inside it.  Call it before the
+ * process allocates device memory.  *out receives a lease that owns the
+ * mappings until kc_va_release.  Returns KC_OK; KC_EINVAL (null out or
+ * regions, n < 1, an empty, null or wrapping region, bad device);
+ * KC_EOVERLAP when the captured ranges cannot be had at their VAs in this
+ * process (in use, or the driver placed the reservation elsewhere; nothing
+ * is relocated, everything made so far is undone and *out stays NULL);
+ * KC_ENOMEM when physical memory could not be allocated; KC_ECUDA for other
+ * driver failures.  The memory is not initialised.
+ * kc_va_lease_bytes: bytes reserved by a lease (granule-rounded), 0 for NULL.
+ * kc_va_release: wait for the device, unmap, free and delete the lease. */
+typedef struct kc_va_lease kc_va_lease;
+KC_API kc_status kc_va_reserve(int device, const kc_buf *regions, int n, kc_va_lease **out);
+KC_API uint64_t kc_va_lease_bytes(const kc_va_lease *lease);
+KC_API void kc_va_release(kc_va_lease *lease);
+
 /* ---- batched form --------------------------------------------------------
  * The operations above launch a few kernels per call; validating thousands
  * of replayed buffers (one tuning campaign re-runs a kernel many times and

@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["kc_api.cu", "k_digest.cu", "k_census.cu", "k_dedup.cu", "k_restore.cu", "k_compare.cu", "k_batch.cu", "kc_noalloc.cu"]
+SOURCES = ["kc_api.cu", "k_digest.cu", "k_census.cu", "k_dedup.cu", "k_restore.cu", "k_compare.cu", "k_batch.cu",
+           "kc_noalloc.cu", "kc_vmm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
                  "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", INCLUDE]

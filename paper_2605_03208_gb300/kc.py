@@ -33,7 +33,8 @@ ESIZE = {U8: 1, RAW: 1, I32: 4, F16: 2, BF16: 2, F32: 4}
 EXPORTS = ["kc_version", "kc_launch_count", "kc_status_name", "kc_last_error", "kc_create", "kc_destroy", "kc_sync",
            "kc_buf_status", "kc_set_digest_shape", "kc_debug_stall_census", "kc_set_trace_events", "kc_get_digest_shape", "kc_page_count",
            "kc_digest", "kc_census", "kc_scan", "kc_dedup", "kc_restore", "kc_compare",
-           "kc_census_static", "kc_batch_run", "kc_poll_flags"]
+           "kc_census_static", "kc_batch_run", "kc_poll_flags", "kc_va_reserve", "kc_va_lease_bytes",
+           "kc_va_release"]
 
 
 class KcBuf(ctypes.Structure):
@@ -120,6 +121,12 @@ def load(build_if_missing: bool = False):
     L.kc_poll_flags.argtypes = [vp, i32, vp]
     L.kc_census_static.restype = st
     L.kc_census_static.argtypes = [B, i32, u64, u64, vp, u64, vp, vp]
+    L.kc_va_reserve.restype = st
+    L.kc_va_reserve.argtypes = [i32, B, i32, ctypes.POINTER(vp)]
+    L.kc_va_lease_bytes.restype = u64
+    L.kc_va_lease_bytes.argtypes = [vp]
+    L.kc_va_release.restype = None
+    L.kc_va_release.argtypes = [vp]
     L.kc_scan.restype = st
     L.kc_scan.argtypes = [vp, B, i32, u32, vp, vp, vp, u64, u64, vp, u64, vp, vp]
     L.kc_dedup.restype = st
@@ -344,6 +351,42 @@ def census_static(regions, win_lo, win_hi, hits_out, cap, counts_out, stream=Non
     b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
     return int(load().kc_census_static(b, len(b), win_lo, win_hi, _ptr(hits_out), cap,
                                        _ptr(counts_out), _stream(stream)))
+
+
+class VaLease:
+    """Device memory mapped at a snapshot's captured VAs (kc_va_reserve);
+    release() (or garbage collection) unmaps it."""
+
+    def __init__(self, handle):
+        self.h = handle
+        self.lib = load()
+
+    @property
+    def bytes(self) -> int:
+        return int(self.lib.kc_va_lease_bytes(self.h)) if self.h else 0
+
+    def release(self):
+        if getattr(self, "h", None):
+            self.lib.kc_va_release(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def va_reserve(device: int, regions) -> "VaLease":
+    """kc_va_reserve: map device memory at exactly the regions' VAs (a list
+    of (base_va, bytes) or a kc_buf array).  Raises KcError with the status
+    (KC_EOVERLAP when a range is already in use in this process)."""
+    b = regions if isinstance(regions, ctypes.Array) else bufs(regions)
+    h = ctypes.c_void_p()
+    s = int(load().kc_va_reserve(device, b, len(b), ctypes.byref(h)))
+    if s != OK:
+        raise KcError(s, "exact-VA reservation failed")
+    return VaLease(h)
 
 
 def launch_count() -> int:

@@ -139,3 +139,20 @@ def test_census_static_argument_checks_are_host_only():
     assert lib.kc_census_static(b, 1, 0, 0, None, 0, None, 0) == kc.EINVAL       # no counts output
     assert lib.kc_census_static(b, 1, 0, 0, None, 5, counts, 0) == kc.EINVAL     # cap without hits
     assert lib.kc_census_static(None, 1, 0, 0, None, 0, counts, 0) == kc.EINVAL  # no regions, n = 1
+
+
+def test_va_reserve_argument_checks_are_host_only():
+    """kc_va_reserve refuses bad arguments before touching a device."""
+    import ctypes
+    lib = kc.load()
+    h = ctypes.c_void_p()
+    b = kc.bufs([(0x7f0000000000, 4096)])
+    assert lib.kc_va_reserve(0, b, 1, None) == kc.EINVAL                       # no lease output
+    assert lib.kc_va_reserve(0, None, 1, ctypes.byref(h)) == kc.EINVAL         # no regions
+    assert lib.kc_va_reserve(0, b, 0, ctypes.byref(h)) == kc.EINVAL            # n = 0
+    assert lib.kc_va_reserve(0, kc.bufs([(0x7f0000000000, 0)]), 1, ctypes.byref(h)) == kc.EINVAL   # empty
+    assert lib.kc_va_reserve(0, kc.bufs([(0, 4096)]), 1, ctypes.byref(h)) == kc.EINVAL             # null base
+    assert lib.kc_va_reserve(0, kc.bufs([(2**64 - 4096, 8192)]), 1, ctypes.byref(h)) == kc.EINVAL  # wraps
+    assert h.value is None
+    assert lib.kc_va_lease_bytes(None) == 0
+    lib.kc_va_release(None)                                                   # a no-op
