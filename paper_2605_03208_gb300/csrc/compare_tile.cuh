@@ -259,6 +259,298 @@ __device__ __forceinline__ void cmp_drain_any(int dt, const SlowQ &q, uint32_t m
     sync();
 }
 
+// ---- warp-streaming comparison -------------------------------------------------
+//
+// A warp streams its own contiguous range of 16-byte vectors of a pair (no
+// block barriers).  A vector whose bits differ anywhere is rare; the lane
+// that finds one does not evaluate it there (the other 31 lanes would idle
+// through the per-element work) but appends the whole vector to the warp's
+// queue in shared memory (one ballot per load, its slot from a popcount);
+// the warp evaluates queued vectors 32 at a time, one per lane, with every
+// lane busy -- NaNs of the vector's equal elements counted, its differing
+// elements widened to FP64 -- when the queue would overflow and when the
+// warp's part of the pair ends.  Equal vectors only have their NaNs counted
+// (two bit tricks per word).
+
+__device__ __forceinline__ CmpAcc cmp_acc_zero() { return CmpAcc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0}; }
+
+// NaN elements of a word: the high bit of each element's slot set by one
+// carry per element ((x & mag) + (mag - inf)) -- an element is NaN iff its
+// magnitude exceeds the infinity pattern -- then counted.
+template <int DT>
+__device__ __forceinline__ uint32_t nan_bits(uint32_t w) {
+    if (DT == KC_F32) return ((w & 0x7fffffffu) + 0x007fffffu) & 0x80000000u;
+    if (DT == KC_BF16) return ((w & 0x7fff7fffu) + 0x007f007fu) & 0x80008000u;
+    if (DT == KC_F16) return ((w & 0x7fff7fffu) + 0x03ff03ffu) & 0x80008000u;
+    return 0u;
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t vec_nans(const uint4 &v) {
+    if (!(DT == KC_F32 || DT == KC_F16 || DT == KC_BF16)) return 0u;
+    const uint32_t a = nan_bits<DT>(v.x), b = nan_bits<DT>(v.y), c = nan_bits<DT>(v.z), d = nan_bits<DT>(v.w);
+    if ((a | b | c | d) == 0u) return 0u;
+    return __popc(a) + __popc(b) + __popc(c) + __popc(d);
+}
+
+struct VecItem {        // a queued vector: its index in the pair and both sides' bits
+    unsigned long long v;
+    uint4 g, w;
+};
+
+struct WarpQ {
+    VecItem *items;     // this warp's slots in shared memory
+    uint32_t cap;       // >= 32
+    uint32_t n;         // queued vectors (the same in every lane)
+    float run_abs;      // running maxima of the warp's proxies (the same in every lane)
+    float run_rel;
+};
+
+// ---- evaluation of queued vectors: FP64 only where it can matter ------------
+//
+// An element whose bits differ is classified from its bits alone: both NaN
+// (equal), one NaN (a mismatch, nan_mismatch), +0 against -0 (equal), or two
+// unequal numbers.  With zero tolerances an unequal pair is always a
+// mismatch (its FP64 difference is never zero: the difference of two
+// distinct values of these types is at least 2^-149), so only the two
+// maxima need FP64 -- and only for elements that can hold them: each
+// element gets fp32 proxies of |a - b| and |a - b| / |b| (relative error
+// below 2^-20, a subnormal reciprocal of |b| > 2^126 included; the integer
+// types' difference is formed exactly first), the
+// warp keeps running maxima of the proxies (over every element it has seen,
+// the batch being evaluated included), and an element is evaluated in FP64
+// only if a proxy reaches the running maximum times (1 - 2^-18), or is
+// infinite or NaN.  An element below that cannot hold the exact FP64
+// maximum, which the evaluated elements therefore contain: the results are
+// bit for bit those of evaluating every element.  With a tolerance, every
+// unequal element is evaluated in FP64 as before.
+
+constexpr float PROXY_KEEP = 1.0f - 1.0f / 262144.0f;   // 1 - 2^-18
+
+template <int DT>
+__device__ __forceinline__ float elem_float(uint32_t bits) {
+    if (DT == KC_F32) return __uint_as_float(bits);
+    if (DT == KC_BF16) return __uint_as_float(bits << 16);
+    if (DT == KC_F16) return __half2float(__ushort_as_half((unsigned short)bits));
+    if (DT == KC_I32) return (float)(int32_t)bits;
+    return (float)bits;
+}
+
+// 0: equal (no contribution but NaN counts), 1: one side NaN, 2: unequal numbers.
+template <int DT>
+__device__ __forceinline__ int elem_class(uint32_t gb, uint32_t wb) {
+    const bool na = bits_nan<DT>(gb), nb = bits_nan<DT>(wb);
+    if (na && nb) return 0;
+    if (na != nb) return 1;
+    if (DT == KC_F32) return ((gb | wb) & 0x7fffffffu) == 0u ? 0 : 2;
+    if (DT == KC_BF16 || DT == KC_F16) return ((gb | wb) & 0x7fffu) == 0u ? 0 : 2;
+    return 2;
+}
+
+// Proxies of |a - b| and |a - b| / |b| for unequal numbers; +inf stands for
+// an infinite or undefined one.
+template <int DT>
+__device__ __forceinline__ void elem_proxies(uint32_t gb, uint32_t wb, float &pa, float &pr) {
+    float d;
+    if (DT == KC_I32) d = (float)llabs((long long)(int32_t)gb - (long long)(int32_t)wb);
+    else if (DT == KC_U8 || DT == KC_RAW) d = (float)(gb > wb ? gb - wb : wb - gb);
+    else d = fabsf(elem_float<DT>(gb) - elem_float<DT>(wb));
+    const float r = d * __frcp_rn(fabsf(elem_float<DT>(wb)));
+    pa = d == d ? d : CUDART_INF_F;
+    pr = r == r ? r : CUDART_INF_F;
+}
+
+// FP64 maxima of one pair of unequal numbers (one IEEE operation each).
+template <int DT>
+__device__ __forceinline__ void elem_maxima(uint32_t gb, uint32_t wb, CmpAcc &acc) {
+    const double a = widen<DT>(gb), b = widen<DT>(wb);
+    const double d = fabs(__dsub_rn(a, b));
+    const double r = (b == 0.0 || isinf(d)) ? CUDART_INF : __ddiv_rn(d, fabs(b));
+    acc.max_abs = d > acc.max_abs ? d : acc.max_abs;
+    acc.max_rel = r > acc.max_rel ? r : acc.max_rel;
+}
+
+// One lane's queued vector, second pass: everything but the screened-out maxima.
+template <int DT>
+__device__ __forceinline__ void vec_eval(const VecItem &it, double atol, double rtol, bool zero_tol, float thr_abs,
+                                         float thr_rel, CmpAcc &acc) {
+    constexpr int per = 4 / esize<DT>();
+    constexpr int PER = 16 / esize<DT>();
+    const uint32_t gw[4] = {it.g.x, it.g.y, it.g.z, it.g.w}, ww[4] = {it.w.x, it.w.y, it.w.z, it.w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int j = 0; j < per; ++j) {
+            const uint32_t ge = elem_of<DT>(gw[k], j), we = elem_of<DT>(ww[k], j);
+            const unsigned long long idx = it.v * PER + k * per + j;
+            if (ge == we) {
+                const uint32_t n = bits_nan<DT>(ge);
+                acc.nan_g += n;
+                acc.nan_w += n;
+                continue;
+            }
+            if (!zero_tol) {
+                cmp_slow<DT>(ge, we, idx, atol, rtol, acc);
+                continue;
+            }
+            const int cls = elem_class<DT>(ge, we);
+            acc.nan_g += bits_nan<DT>(ge);
+            acc.nan_w += bits_nan<DT>(we);
+            if (cls == 0) continue;
+            acc.mism += 1;
+            acc.first = idx < acc.first ? idx : acc.first;
+            if (cls == 1) {
+                acc.nan_m += 1;
+                continue;
+            }
+            float pa, pr;
+            elem_proxies<DT>(ge, we, pa, pr);
+            if (!(pa < thr_abs) || !(pr < thr_rel)) elem_maxima<DT>(ge, we, acc);
+        }
+    }
+}
+
+// First pass: the largest proxies of a lane's queued vector.
+template <int DT>
+__device__ __forceinline__ void vec_proxy_max(const VecItem &it, float &ma, float &mr) {
+    constexpr int per = 4 / esize<DT>();
+    const uint32_t gw[4] = {it.g.x, it.g.y, it.g.z, it.g.w}, ww[4] = {it.w.x, it.w.y, it.w.z, it.w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int j = 0; j < per; ++j) {
+            const uint32_t ge = elem_of<DT>(gw[k], j), we = elem_of<DT>(ww[k], j);
+            if (ge == we || elem_class<DT>(ge, we) != 2) continue;
+            float pa, pr;
+            elem_proxies<DT>(ge, we, pa, pr);
+            ma = fmaxf(ma, pa);
+            mr = fmaxf(mr, pr);
+        }
+    }
+}
+
+// n queued vectors, 32 at a time (one per lane, every lane busy).  run_abs
+// / run_rel: the warp's running proxy maxima, updated.  Returns this lane's
+// share of the accumulators.
+template <int DT>
+__device__ __noinline__ CmpAcc wq_eval(const VecItem *items, uint32_t n, double atol, double rtol, float *run) {
+    const uint32_t FULL = 0xffffffffu;
+    const bool zero_tol = atol == 0.0 && rtol == 0.0;
+    CmpAcc a = cmp_acc_zero();
+    float run_abs = run[0], run_rel = run[1];
+    __syncwarp();
+    for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+        const uint32_t i = b0 + lane_id();
+        VecItem it;
+        float ma = 0.0f, mr = 0.0f;
+        if (i < n) {
+            it = items[i];
+            if (zero_tol) vec_proxy_max<DT>(it, ma, mr);
+        }
+        // proxies are >= 0 (or +inf), so their bit patterns order like their values
+        run_abs = fmaxf(run_abs, __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(ma))));
+        run_rel = fmaxf(run_rel, __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mr))));
+        if (i < n) vec_eval<DT>(it, atol, rtol, zero_tol, run_abs * PROXY_KEEP, run_rel * PROXY_KEEP, a);
+    }
+    __syncwarp();
+    run[0] = run_abs;
+    run[1] = run_rel;
+    return a;
+}
+
+__device__ __forceinline__ void cmp_acc_merge(CmpAcc &a, const CmpAcc &b) {
+    a.mism += b.mism;
+    a.first = b.first < a.first ? b.first : a.first;
+    a.nan_g += b.nan_g;
+    a.nan_w += b.nan_w;
+    a.nan_m += b.nan_m;
+    a.max_abs = b.max_abs > a.max_abs ? b.max_abs : a.max_abs;
+    a.max_rel = b.max_rel > a.max_rel ? b.max_rel : a.max_rel;
+}
+
+template <int DT>
+__device__ __forceinline__ void wq_drain(WarpQ &q, double atol, double rtol, CmpAcc &acc) {
+    if (q.n == 0) return;
+    float run[2] = {q.run_abs, q.run_rel};
+    cmp_acc_merge(acc, wq_eval<DT>(q.items, q.n, atol, rtol, run));
+    q.run_abs = run[0];
+    q.run_rel = run[1];
+    q.n = 0;
+}
+
+// One vector per lane (vector index v, `differs` when its bits differ):
+// NaNs of equal vectors are counted; differing ones are queued.  All lanes
+// call it.
+template <int DT>
+__device__ __forceinline__ void vec_step(WarpQ &q, const uint4 &g, const uint4 &w, unsigned long long v,
+                                         bool valid, double atol, double rtol, CmpAcc &acc) {
+    const bool differs = valid && (g.x != w.x || g.y != w.y || g.z != w.z || g.w != w.w);
+    if (valid && !differs) {
+        const uint32_t n = vec_nans<DT>(g);
+        acc.nan_g += n;
+        acc.nan_w += n;
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, differs);
+    if (b == 0u) return;
+    if (q.n + 32 > q.cap) wq_drain<DT>(q, atol, rtol, acc);
+    if (differs) q.items[q.n + __popc(b & lanemask_lt())] = VecItem{v, g, w};
+    q.n += __popc(b);
+}
+
+// Vectors [va, vb) of a pair (16-byte units from its start), U loads of
+// each buffer in flight per lane; all 32 lanes call it.
+template <int DT, int U>
+__device__ __forceinline__ void warp_compare_range(const CmpPair &pr, uint64_t va, uint64_t vb, double atol,
+                                                   double rtol, CmpAcc &acc, WarpQ &q) {
+    const uint8_t *g = reinterpret_cast<const uint8_t *>(pr.got);
+    const uint8_t *w = reinterpret_cast<const uint8_t *>(pr.want);
+    const uint64_t lane = lane_id();
+    uint64_t v = va;
+    for (; v + 32 * U <= vb; v += 32 * U) {
+        uint4 gv[U], wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            gv[u] = ldg_stream(g + 16 * (v + 32 * u + lane));
+            wv[u] = ldg_stream(w + 16 * (v + 32 * u + lane));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) vec_step<DT>(q, gv[u], wv[u], v + 32 * u + lane, true, atol, rtol, acc);
+    }
+    for (; v < vb; v += 32) {
+        const bool ok = v + lane < vb;
+        uint4 gv = make_uint4(0, 0, 0, 0), wv = gv;
+        if (ok) {
+            gv = ldg_stream(g + 16 * (v + lane));
+            wv = ldg_stream(w + 16 * (v + lane));
+        }
+        vec_step<DT>(q, gv, wv, v + lane, ok, atol, rtol, acc);
+    }
+}
+
+// The < 16-byte end of a pair, element by element (lane e takes element e).
+template <int DT>
+__device__ __forceinline__ void warp_compare_tail(const CmpPair &pr, double atol, double rtol, CmpAcc &acc,
+                                                  WarpQ &) {
+    constexpr int ES = esize<DT>();
+    const uint64_t nbytes = pr.nelem * ES;
+    const uint64_t b = (nbytes & ~15ull) + (uint64_t)lane_id() * ES;
+    if (b >= nbytes) return;
+    const uint8_t *g = reinterpret_cast<const uint8_t *>(pr.got) + b;
+    const uint8_t *w = reinterpret_cast<const uint8_t *>(pr.want) + b;
+    uint32_t gb = 0, wb = 0;
+    for (int j = 0; j < ES; ++j) {
+        gb |= (uint32_t)g[j] << (8 * j);
+        wb |= (uint32_t)w[j] << (8 * j);
+    }
+    if (gb == wb) {
+        const uint32_t n = bits_nan<DT>(gb);
+        acc.nan_g += n;
+        acc.nan_w += n;
+    } else {
+        cmp_slow<DT>(gb, wb, b / ES, atol, rtol, acc);
+    }
+}
+
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 // Reduce a warp's accumulators and merge them into the pair's record with

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchJob *__restrict__
             pr.tile_first = 0;
             pr.dtype = J.dtype;
             pr.lost = 0;
+            pr.vec_first = 0;
             CmpAcc acc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0};
             const uint64_t tiles = (J.bytes + CMP_TILE_BYTES - 1) / CMP_TILE_BYTES;
             const uint64_t t0 = (R.first + k) * (BATCH_CMP_ITEM_BYTES / CMP_TILE_BYTES);

@@ -29,6 +29,7 @@ cudaError_t setup_kernels() {
     cudaError_t e = setup_digest_kernels();
     if (e != cudaSuccess) return e;
     if ((e = setup_dedup_kernels()) != cudaSuccess) return e;
+    if ((e = setup_compare_kernels()) != cudaSuccess) return e;
     return setup_batch_kernels();
 }
 
@@ -69,6 +70,7 @@ struct Tables {
     bool pinned = false;        // read by a captured graph: never recycled
     std::vector<int> buf_status;
     CensusArgs ca{};
+    CmpGroups groups{};         // comparison: pairs grouped by dtype
     const Region *regions() const { return static_cast<const Region *>(part[TP_REGIONS]); }
     const uint64_t *page_first() const { return static_cast<const uint64_t *>(part[TP_PAGEFIRST]); }
     const Range *ranges() const { return static_cast<const Range *>(part[TP_RANGES]); }
@@ -805,12 +807,32 @@ KC_API kc_status kc_compare(kc_ctx *c, const kc_buf *got, const kc_buf *want, in
                 p.tile_first = tiles;
                 p.dtype = dt == KC_RAW ? KC_U8 : dt;
                 p.lost = ((got[k].flags | want[k].flags) & KC_BUF_LOST) ? 1 : 0;
+                p.out_index = (uint32_t)k;
+                p.pad = 0;
                 if (p.lost) {
                     tb.any_lost = true;
                     tb.buf_status[k] = KC_EBUF;
                 }
                 tiles += (got[k].bytes + CMP_TILE_BYTES - 1) / CMP_TILE_BYTES;
             }
+            // group by dtype (stable), vectors numbered within each group
+            std::stable_sort(pairs.begin(), pairs.end(),
+                             [](const CmpPair &a, const CmpPair &b) { return a.dtype < b.dtype; });
+            CmpGroups &gr = tb.groups;
+            gr = CmpGroups{};
+            int at = 0;
+            for (int d = 0; d < 6; ++d) {
+                gr.gfirst[d] = at;
+                uint64_t v = 0;
+                while (at < npairs && pairs[at].dtype == d) {
+                    const uint64_t es = (d == KC_F32 || d == KC_I32) ? 4 : (d == KC_F16 || d == KC_BF16) ? 2 : 1;
+                    pairs[at].vec_first = v;
+                    v += pairs[at].nelem * es / 16;
+                    ++at;
+                }
+                gr.gvec[d] = v;
+            }
+            gr.gfirst[6] = at;
             tb.units = tiles;
             tb.n = npairs;
             put(parts[TP_PAIRS], pairs);
@@ -820,7 +842,7 @@ KC_API kc_status kc_compare(kc_ctx *c, const kc_buf *got, const kc_buf *want, in
     if (s != KC_OK) return s;
     {
         Trace tr(c, st);
-        KC_CHECK(c, launch_compare(t->pairs(), npairs, t->units, atol, rtol, d_out, nullptr, c->sms, st), "compare");
+        KC_CHECK(c, launch_compare(t->pairs(), npairs, t->groups, atol, rtol, d_out, c->sms, st), "compare");
     }
     touch(c, t, st);
     return t->any_lost ? fail(c, KC_EBUF, "one or more pairs were marked lost") : KC_OK;

@@ -199,10 +199,20 @@ struct CmpPair {
     uint64_t tile_first;   // first global tile id of this pair
     int32_t dtype;
     int32_t lost;
+    uint64_t vec_first;    // first of this pair's whole 16-byte vectors among its dtype group's
+    uint32_t out_index;    // index of the pair's record in the caller's output
+    uint32_t pad;
 };
-cudaError_t launch_compare(const CmpPair *pairs, int npairs, uint64_t ntiles, double atol,
-                           double rtol, kc_cmp_result *out, const int32_t *init_status,
-                           int sms, cudaStream_t st);
+// Pairs sorted by dtype: group d (dtype d) is pairs [gfirst[d], gfirst[d+1])
+// with gvec[d] whole 16-byte vectors in all (vec_first counts within the
+// group); each record goes to out[pair.out_index].
+struct CmpGroups {
+    int gfirst[7];
+    uint64_t gvec[6];
+};
+cudaError_t launch_compare(const CmpPair *pairs, int npairs, const CmpGroups &groups, double atol, double rtol,
+                           kc_cmp_result *out, int sms, cudaStream_t st);
+cudaError_t setup_compare_kernels();
 constexpr uint32_t CMP_TILE_BYTES = 16 * 1024;
 
 // Batched form (k_batch.cu).  A job is one buffer to digest and/or compare,
