@@ -11,14 +11,17 @@
 // __ddiv_rn, __dmul_rn, __dadd_rn: no FMA contraction), hence identical to
 // any other correctly rounded evaluation.
 //
-// Differing elements are rare and scattered, so evaluating each where it is
-// found would run the FP64 sequence once per element with one lane active;
+// Two bodies use this.  The batched kernel compares tiles with a CTA: its
+// differing elements are queued (index and both bit patterns, in shared
+// memory) and evaluated at the end of the tile with every lane busy, since
 // on this part a warp's FP64 instruction costs the same whatever its active
-// lanes.  They are queued instead (index and both bit patterns, in shared
-// memory) and the queue is evaluated at the end of the tile with every lane
-// busy.  What is accumulated -- counts, the smallest index, maxima -- does
-// not depend on the order, so the results are unchanged.  An element that
-// finds the queue full is evaluated where it is.
+// lanes; an element that finds the queue full is evaluated where it is.
+// The comparison kernel streams with warps (warp_compare_range): with
+// tolerances it queues differing vectors per warp the same way; with zero
+// tolerances it classifies them where they are found and uses FP64 only for
+// the few elements that can hold the maxima (below).  What is accumulated
+// -- counts, the smallest index, maxima -- does not depend on the order, so
+// the results are unchanged.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -304,26 +307,30 @@ struct WarpQ {
     uint32_t n;         // queued vectors (the same in every lane)
     float run_abs;      // running maxima of the warp's proxies (the same in every lane)
     float run_rel;
+    uint32_t *gate;     // the pair's proxy maxima over every warp (2 x fp32 bits, global), or null
 };
 
-// ---- evaluation of queued vectors: FP64 only where it can matter ------------
+// ---- zero tolerances: FP64 only where it can matter -------------------------
 //
 // An element whose bits differ is classified from its bits alone: both NaN
 // (equal), one NaN (a mismatch, nan_mismatch), +0 against -0 (equal), or two
 // unequal numbers.  With zero tolerances an unequal pair is always a
 // mismatch (its FP64 difference is never zero: the difference of two
 // distinct values of these types is at least 2^-149), so only the two
-// maxima need FP64 -- and only for elements that can hold them: each
+// maxima need FP64 -- and only for elements that can hold them.  Each
 // element gets fp32 proxies of |a - b| and |a - b| / |b| (relative error
 // below 2^-20, a subnormal reciprocal of |b| > 2^126 included; the integer
-// types' difference is formed exactly first), the
-// warp keeps running maxima of the proxies (over every element it has seen,
-// the batch being evaluated included), and an element is evaluated in FP64
-// only if a proxy reaches the running maximum times (1 - 2^-18), or is
-// infinite or NaN.  An element below that cannot hold the exact FP64
-// maximum, which the evaluated elements therefore contain: the results are
-// bit for bit those of evaluating every element.  With a tolerance, every
-// unequal element is evaluated in FP64 as before.
+// types' difference is formed exactly first).  The warp keeps running
+// maxima of its proxies and shares them through the pair's gate (a global
+// maximum every warp of the grid reads and raises), and an element is
+// evaluated in FP64 only if a proxy reaches the larger of the two times
+// (1 - 2^-18), or is infinite or NaN.  An element below that threshold is
+// smaller, exactly, than an element some warp has seen, so it cannot hold
+// the exact FP64 maximum; by induction the element with the largest proxy
+// is always evaluated, and the results are bit for bit those of evaluating
+// every element.  (On this part a warp's FP64 instruction holds the FP64
+// pipe for about sixteen cycles, so this matters: evaluating every
+// differing element cost 0.4-0.7 ns of whole-GPU time each.)
 
 constexpr float PROXY_KEEP = 1.0f - 1.0f / 262144.0f;   // 1 - 2^-18
 
@@ -370,10 +377,15 @@ __device__ __forceinline__ void elem_maxima(uint32_t gb, uint32_t wb, CmpAcc &ac
     acc.max_rel = r > acc.max_rel ? r : acc.max_rel;
 }
 
-// One lane's queued vector, second pass: everything but the screened-out maxima.
+// ---- with tolerances: differing vectors queued, evaluated in FP64 ----------
+//
+// The mismatch test d > atol + rtol |b| needs every unequal element's FP64
+// values, so differing vectors are queued per warp and evaluated 32 at a
+// time with every lane busy (one FP64 sequence per element, none idle).
+
+// One lane's queued vector.
 template <int DT>
-__device__ __forceinline__ void vec_eval(const VecItem &it, double atol, double rtol, bool zero_tol, float thr_abs,
-                                         float thr_rel, CmpAcc &acc) {
+__device__ __forceinline__ void vec_eval(const VecItem &it, double atol, double rtol, CmpAcc &acc) {
     constexpr int per = 4 / esize<DT>();
     constexpr int PER = 16 / esize<DT>();
     const uint32_t gw[4] = {it.g.x, it.g.y, it.g.z, it.g.w}, ww[4] = {it.w.x, it.w.y, it.w.z, it.w.w};
@@ -382,79 +394,24 @@ __device__ __forceinline__ void vec_eval(const VecItem &it, double atol, double 
 #pragma unroll
         for (int j = 0; j < per; ++j) {
             const uint32_t ge = elem_of<DT>(gw[k], j), we = elem_of<DT>(ww[k], j);
-            const unsigned long long idx = it.v * PER + k * per + j;
             if (ge == we) {
                 const uint32_t n = bits_nan<DT>(ge);
                 acc.nan_g += n;
                 acc.nan_w += n;
                 continue;
             }
-            if (!zero_tol) {
-                cmp_slow<DT>(ge, we, idx, atol, rtol, acc);
-                continue;
-            }
-            const int cls = elem_class<DT>(ge, we);
-            acc.nan_g += bits_nan<DT>(ge);
-            acc.nan_w += bits_nan<DT>(we);
-            if (cls == 0) continue;
-            acc.mism += 1;
-            acc.first = idx < acc.first ? idx : acc.first;
-            if (cls == 1) {
-                acc.nan_m += 1;
-                continue;
-            }
-            float pa, pr;
-            elem_proxies<DT>(ge, we, pa, pr);
-            if (!(pa < thr_abs) || !(pr < thr_rel)) elem_maxima<DT>(ge, we, acc);
+            cmp_slow<DT>(ge, we, it.v * PER + k * per + j, atol, rtol, acc);
         }
     }
 }
 
-// First pass: the largest proxies of a lane's queued vector.
+// n queued vectors, 32 at a time; returns this lane's share of the accumulators.
 template <int DT>
-__device__ __forceinline__ void vec_proxy_max(const VecItem &it, float &ma, float &mr) {
-    constexpr int per = 4 / esize<DT>();
-    const uint32_t gw[4] = {it.g.x, it.g.y, it.g.z, it.g.w}, ww[4] = {it.w.x, it.w.y, it.w.z, it.w.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-#pragma unroll
-        for (int j = 0; j < per; ++j) {
-            const uint32_t ge = elem_of<DT>(gw[k], j), we = elem_of<DT>(ww[k], j);
-            if (ge == we || elem_class<DT>(ge, we) != 2) continue;
-            float pa, pr;
-            elem_proxies<DT>(ge, we, pa, pr);
-            ma = fmaxf(ma, pa);
-            mr = fmaxf(mr, pr);
-        }
-    }
-}
-
-// n queued vectors, 32 at a time (one per lane, every lane busy).  run_abs
-// / run_rel: the warp's running proxy maxima, updated.  Returns this lane's
-// share of the accumulators.
-template <int DT>
-__device__ __noinline__ CmpAcc wq_eval(const VecItem *items, uint32_t n, double atol, double rtol, float *run) {
-    const uint32_t FULL = 0xffffffffu;
-    const bool zero_tol = atol == 0.0 && rtol == 0.0;
+__device__ __noinline__ CmpAcc wq_eval(const VecItem *items, uint32_t n, double atol, double rtol) {
     CmpAcc a = cmp_acc_zero();
-    float run_abs = run[0], run_rel = run[1];
     __syncwarp();
-    for (uint32_t b0 = 0; b0 < n; b0 += 32) {
-        const uint32_t i = b0 + lane_id();
-        VecItem it;
-        float ma = 0.0f, mr = 0.0f;
-        if (i < n) {
-            it = items[i];
-            if (zero_tol) vec_proxy_max<DT>(it, ma, mr);
-        }
-        // proxies are >= 0 (or +inf), so their bit patterns order like their values
-        run_abs = fmaxf(run_abs, __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(ma))));
-        run_rel = fmaxf(run_rel, __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mr))));
-        if (i < n) vec_eval<DT>(it, atol, rtol, zero_tol, run_abs * PROXY_KEEP, run_rel * PROXY_KEEP, a);
-    }
+    for (uint32_t i = lane_id(); i < n; i += 32) vec_eval<DT>(items[i], atol, rtol, a);
     __syncwarp();
-    run[0] = run_abs;
-    run[1] = run_rel;
     return a;
 }
 
@@ -471,17 +428,115 @@ __device__ __forceinline__ void cmp_acc_merge(CmpAcc &a, const CmpAcc &b) {
 template <int DT>
 __device__ __forceinline__ void wq_drain(WarpQ &q, double atol, double rtol, CmpAcc &acc) {
     if (q.n == 0) return;
-    float run[2] = {q.run_abs, q.run_rel};
-    cmp_acc_merge(acc, wq_eval<DT>(q.items, q.n, atol, rtol, run));
-    q.run_abs = run[0];
-    q.run_rel = run[1];
+    cmp_acc_merge(acc, wq_eval<DT>(q.items, q.n, atol, rtol));
     q.n = 0;
 }
 
-// One vector per lane (vector index v, `differs` when its bits differ):
-// NaNs of equal vectors are counted; differing ones are queued.  All lanes
-// call it.
+// ---- zero tolerances: differing vectors handled where they are found ---------
+//
+// With atol == rtol == 0 an unequal element is a mismatch from its bits
+// alone, so a lane classifies the elements of its differing vector at once
+// (counts, first index, NaN rules) and takes the largest proxies.  Only when
+// the warp's largest proxy reaches its running threshold (the warp's and the
+// pair's gate maxima times 1 - 2^-18) does the warp publish it to the gate,
+// refresh the threshold from it and evaluate the elements still above it in
+// FP64.  Such records are few (a running maximum over the pair), so FP64
+// work is spread thinly over the kernel instead of being queued to its end.
+
+// Lane-local pass over one differing vector: everything but the FP64
+// maxima; ma / mr receive the largest proxies of its unequal numbers.
 template <int DT>
+__device__ __forceinline__ void vec_classify(const uint4 &g, const uint4 &w, unsigned long long v, CmpAcc &acc,
+                                             float &ma, float &mr) {
+    constexpr int per = 4 / esize<DT>();
+    constexpr int PER = 16 / esize<DT>();
+    const uint32_t gw[4] = {g.x, g.y, g.z, g.w}, ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (gw[k] == ww[k]) {
+            const uint32_t n = __popc(nan_bits<DT>(gw[k]));
+            acc.nan_g += n;
+            acc.nan_w += n;
+            continue;
+        }
+#pragma unroll
+        for (int j = 0; j < per; ++j) {
+            const uint32_t ge = elem_of<DT>(gw[k], j), we = elem_of<DT>(ww[k], j);
+            const uint32_t ng = bits_nan<DT>(ge), nw = bits_nan<DT>(we);
+            acc.nan_g += ng;
+            acc.nan_w += nw;
+            if (ge == we) continue;
+            const int cls = elem_class<DT>(ge, we);
+            if (cls == 0) continue;
+            const unsigned long long idx = v * PER + k * per + j;
+            acc.mism += 1;
+            acc.first = idx < acc.first ? idx : acc.first;
+            if (cls == 1) {
+                acc.nan_m += 1;
+                continue;
+            }
+            float pa, pr;
+            elem_proxies<DT>(ge, we, pa, pr);
+            ma = fmaxf(ma, pa);
+            mr = fmaxf(mr, pr);
+        }
+    }
+}
+
+// FP64 maxima of the unequal numbers of one vector whose proxies reach the thresholds.
+template <int DT>
+__device__ __forceinline__ void vec_exact_max(const uint4 &g, const uint4 &w, float ta, float tr, CmpAcc &acc) {
+    constexpr int per = 4 / esize<DT>();
+    const uint32_t gw[4] = {g.x, g.y, g.z, g.w}, ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (gw[k] == ww[k]) continue;
+#pragma unroll
+        for (int j = 0; j < per; ++j) {
+            const uint32_t ge = elem_of<DT>(gw[k], j), we = elem_of<DT>(ww[k], j);
+            if (ge == we || elem_class<DT>(ge, we) != 2) continue;
+            float pa, pr;
+            elem_proxies<DT>(ge, we, pa, pr);
+            if (!(pa < ta) || !(pr < tr)) elem_maxima<DT>(ge, we, acc);
+        }
+    }
+}
+
+// A warp step with at least one differing vector (zero tolerances); all
+// lanes call it.  The warp's running proxy maxima live in q; the pair's gate
+// is read with a plain load and raised (atomic max, no return) only by a
+// warp holding a larger maximum, so warps do not queue on one address.
+template <int DT>
+__device__ __forceinline__ void vec_found(const uint4 &g, const uint4 &w, unsigned long long v, bool differs,
+                                          WarpQ &q, CmpAcc &acc) {
+    const uint32_t FULL = 0xffffffffu;
+    float ma = 0.0f, mr = 0.0f;
+    if (differs) vec_classify<DT>(g, w, v, acc, ma, mr);
+    // proxies are >= 0 (or +inf), so their bit patterns order like their values
+    const float wa = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(ma)));
+    const float wr = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mr)));
+    if (!(wa > 0.0f) || (wa < q.run_abs * PROXY_KEEP && wr < q.run_rel * PROXY_KEEP)) return;
+    float ra = fmaxf(q.run_abs, wa), rr = fmaxf(q.run_rel, wr);
+    if (q.gate) {
+        uint32_t ga = 0u, gr = 0u;
+        if (lane_id() == 0) {
+            ga = *reinterpret_cast<volatile uint32_t *>(q.gate);
+            gr = *reinterpret_cast<volatile uint32_t *>(q.gate + 1);
+            if (__float_as_uint(ra) > ga) atomicMax(q.gate, __float_as_uint(ra));
+            if (__float_as_uint(rr) > gr) atomicMax(q.gate + 1, __float_as_uint(rr));
+        }
+        ra = fmaxf(ra, __uint_as_float(__shfl_sync(FULL, ga, 0)));
+        rr = fmaxf(rr, __uint_as_float(__shfl_sync(FULL, gr, 0)));
+    }
+    if (differs) vec_exact_max<DT>(g, w, ra * PROXY_KEEP, rr * PROXY_KEEP, acc);
+    q.run_abs = ra;
+    q.run_rel = rr;
+}
+
+// One vector per lane (vector index v, `differs` when its bits differ):
+// NaNs of equal vectors are counted; differing ones are handled at once
+// (ZT: zero tolerances) or queued.  All lanes call it.
+template <int DT, bool ZT>
 __device__ __forceinline__ void vec_step(WarpQ &q, const uint4 &g, const uint4 &w, unsigned long long v,
                                          bool valid, double atol, double rtol, CmpAcc &acc) {
     const bool differs = valid && (g.x != w.x || g.y != w.y || g.z != w.z || g.w != w.w);
@@ -492,6 +547,10 @@ __device__ __forceinline__ void vec_step(WarpQ &q, const uint4 &g, const uint4 &
     }
     const uint32_t b = __ballot_sync(0xffffffffu, differs);
     if (b == 0u) return;
+    if (ZT) {
+        vec_found<DT>(g, w, v, differs, q, acc);
+        return;
+    }
     if (q.n + 32 > q.cap) wq_drain<DT>(q, atol, rtol, acc);
     if (differs) q.items[q.n + __popc(b & lanemask_lt())] = VecItem{v, g, w};
     q.n += __popc(b);
@@ -499,7 +558,7 @@ __device__ __forceinline__ void vec_step(WarpQ &q, const uint4 &g, const uint4 &
 
 // Vectors [va, vb) of a pair (16-byte units from its start), U loads of
 // each buffer in flight per lane; all 32 lanes call it.
-template <int DT, int U>
+template <int DT, int U, bool ZT>
 __device__ __forceinline__ void warp_compare_range(const CmpPair &pr, uint64_t va, uint64_t vb, double atol,
                                                    double rtol, CmpAcc &acc, WarpQ &q) {
     const uint8_t *g = reinterpret_cast<const uint8_t *>(pr.got);
@@ -513,8 +572,38 @@ __device__ __forceinline__ void warp_compare_range(const CmpPair &pr, uint64_t v
             gv[u] = ldg_stream(g + 16 * (v + 32 * u + lane));
             wv[u] = ldg_stream(w + 16 * (v + 32 * u + lane));
         }
+        if (ZT) {
+            // one vote per block; the rare handling appears once in the code
+            uint32_t dm = 0u;
 #pragma unroll
-        for (int u = 0; u < U; ++u) vec_step<DT>(q, gv[u], wv[u], v + 32 * u + lane, true, atol, rtol, acc);
+            for (int u = 0; u < U; ++u) {
+                const bool d = gv[u].x != wv[u].x || gv[u].y != wv[u].y || gv[u].z != wv[u].z || gv[u].w != wv[u].w;
+                if (!d) {
+                    const uint32_t n = vec_nans<DT>(gv[u]);
+                    acc.nan_g += n;
+                    acc.nan_w += n;
+                }
+                dm |= (uint32_t)d << u;
+            }
+            if (__any_sync(0xffffffffu, dm != 0u)) {
+#pragma unroll 1
+                for (int u = 0; u < U; ++u) {
+                    const bool d = (dm >> u) & 1u;
+                    if (!__any_sync(0xffffffffu, d)) continue;
+                    uint4 gs = gv[0], ws = wv[0];
+#pragma unroll
+                    for (int t = 1; t < U; ++t)
+                        if (u == t) {
+                            gs = gv[t];
+                            ws = wv[t];
+                        }
+                    vec_found<DT>(gs, ws, v + 32 * u + lane, d, q, acc);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) vec_step<DT, ZT>(q, gv[u], wv[u], v + 32 * u + lane, true, atol, rtol, acc);
+        }
     }
     for (; v < vb; v += 32) {
         const bool ok = v + lane < vb;
@@ -523,7 +612,7 @@ __device__ __forceinline__ void warp_compare_range(const CmpPair &pr, uint64_t v
             gv = ldg_stream(g + 16 * (v + lane));
             wv = ldg_stream(w + 16 * (v + lane));
         }
-        vec_step<DT>(q, gv, wv, v + lane, ok, atol, rtol, acc);
+        vec_step<DT, ZT>(q, gv, wv, v + lane, ok, atol, rtol, acc);
     }
 }
 

@@ -840,9 +840,13 @@ KC_API kc_status kc_compare(kc_ctx *c, const kc_buf *got, const kc_buf *want, in
         },
         &t);
     if (s != KC_OK) return s;
+    void *gates = nullptr;
+    if ((s = scratch(c, (size_t)npairs * 8, st, &gates)) != KC_OK) return s;
     {
         Trace tr(c, st);
-        KC_CHECK(c, launch_compare(t->pairs(), npairs, t->groups, atol, rtol, d_out, c->sms, st), "compare");
+        KC_CHECK(c, launch_compare(t->pairs(), npairs, t->groups, atol, rtol, d_out, static_cast<uint32_t *>(gates),
+                                   c->sms, st),
+                 "compare");
     }
     touch(c, t, st);
     return t->any_lost ? fail(c, KC_EBUF, "one or more pairs were marked lost") : KC_OK;

@@ -210,8 +210,9 @@ struct CmpGroups {
     int gfirst[7];
     uint64_t gvec[6];
 };
+// gates: 2 x npairs words of device scratch (the pairs' proxy maxima).
 cudaError_t launch_compare(const CmpPair *pairs, int npairs, const CmpGroups &groups, double atol, double rtol,
-                           kc_cmp_result *out, int sms, cudaStream_t st);
+                           kc_cmp_result *out, uint32_t *gates, int sms, cudaStream_t st);
 cudaError_t setup_compare_kernels();
 constexpr uint32_t CMP_TILE_BYTES = 16 * 1024;
 

@@ -390,7 +390,8 @@ def test_compare_tolerances(ctx, atol, rtol):
         _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype, atol, rtol))
 
 
-def test_compare_special_values(ctx):
+@pytest.mark.parametrize("tol", [1e30, 0.0])
+def test_compare_special_values(ctx, tol):
     inf, nan = np.inf, np.nan
     g = np.array([0.0, -0.0, inf, inf, -inf, 1.0, nan, nan, 2.0, 3.0, 0.0, 1e-45, 5, 6, 7, 8, 9],
                  dtype=np.float32)
@@ -401,9 +402,65 @@ def test_compare_special_values(ctx):
     pairs = [W.Pair(g, w, W.DT_F32), W.Pair(h16, w16, W.DT_F16), W.Pair(h16, w16, W.DT_BF16),
              W.Pair(np.array([-2**31, 2**31 - 1, 0, 1], np.int32),
                     np.array([2**31 - 1, -2**31, 0, 1], np.int32), W.DT_I32)]
-    recs = _cmp_gpu(ctx, pairs, 1e30, 1e30)
+    recs = _cmp_gpu(ctx, pairs, tol, tol)
     for rec, p in zip(recs, pairs):
-        _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype, 1e30, 1e30))
+        _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype, tol, tol))
+
+
+def _near_tie_f32(rng, n, k):
+    """k scattered elements of an f32 pair whose relative differences agree
+    to about 2^-23 (fp32 cannot order them, FP64 can), plus their indices."""
+    want = rng.standard_normal(n).astype(np.float32)
+    got = want.copy()
+    idx = np.sort(rng.choice(n, k, replace=False))
+    b = (1.0 + rng.integers(0, 4096, k) * 2.0**-23).astype(np.float32)   # distinct values just above 1
+    want[idx] = b
+    got[idx] = (b.astype(np.float64) + 2.0**-10).astype(np.float32)      # exact: the same difference
+    return got, want, idx
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_compare_zero_tolerance_maxima_over_many_warps(ctx, seed):
+    """Zero tolerances: many scattered differences of every size, near-ties
+    that only FP64 orders, NaN / inf / zero / subnormal cases -- the exact
+    maxima must come out whichever warps see which elements first."""
+    rng = np.random.default_rng(seed + 77)
+    n = 1 << 22
+    got, want, _ = _near_tie_f32(rng, n, 3000)
+    idx = rng.choice(n, 200_000, replace=False)
+    got[idx] = (want[idx] * (1 + rng.uniform(-1e-3, 1e-3, idx.size))).astype(np.float32)
+    sp = rng.choice(n, 64, replace=False)
+    got[sp[:8]] = np.nan
+    want[sp[8:16]] = np.nan
+    got[sp[16:24]], want[sp[16:24]] = np.nan, np.nan
+    got[sp[24:32]], want[sp[24:32]] = 0.0, -0.0
+    got[sp[32:40]] = np.inf
+    got[sp[40:48]], want[sp[40:48]] = 1e-45, 0.0
+    got[sp[48:56]], want[sp[48:56]] = 3e38, -3e38
+    want[sp[56:64]] = 0.0
+    f32 = W.Pair(got, want, W.DT_F32)
+    w32 = rng.integers(-2**31, 2**31, n, dtype=np.int64).astype(np.int32)
+    g32 = w32.copy()
+    j = rng.choice(n, 50_000, replace=False)
+    g32[j] = rng.integers(-2**31, 2**31, j.size, dtype=np.int64).astype(np.int32)
+    g32[j[:10]], w32[j[:10]] = 2**31 - 1, -2**31
+    g32[j[10:20]], w32[j[10:20]] = 5, 0
+    i32 = W.Pair(g32, w32, W.DT_I32)
+    w8 = rng.integers(0, 256, n, dtype=np.uint8)
+    g8 = w8.copy()
+    j = rng.choice(n, 100_000, replace=False)
+    g8[j] = rng.integers(0, 256, j.size, dtype=np.uint8)
+    u8 = W.Pair(g8, w8, W.DT_U8)
+    fb = rng.standard_normal(n).astype(np.float32)
+    wb16 = (fb.view(np.uint32) >> 16).astype(np.uint16)
+    gb16 = wb16.copy()
+    j = rng.choice(n, 29_360, replace=False)
+    gb16[j] ^= np.uint16(1)
+    bf = W.Pair(gb16, wb16, W.DT_BF16)
+    pairs = [f32, i32, u8, bf]
+    recs = _cmp_gpu(ctx, pairs)
+    for rec, p in zip(recs, pairs):
+        _assert_records_equal(rec, oracle.compare(p.got, p.want, p.dtype))
 
 
 # ---------------------------------------------------------------- failures
