@@ -599,6 +599,10 @@ def run_kc(args):
         line = {"metric": METRIC, "note": "headline measurement skipped (--no-main)"}
         if not args.no_llama:
             line["llama"] = run_llama_section(args, ctx, device, peak, peak_kind)
+        if not args.no_batched:
+            line["batched"] = run_batched_section(args, device, peak)
+        if not args.no_served:
+            line["served"] = run_served_section(args, device)
         if rank == 0:
             print(json.dumps(line))
         ctx.close()

@@ -381,9 +381,12 @@ KC_API void kc_va_release(kc_va_lease *lease);
  * be read (outputs marked as by the single-operation calls).
  *
  * work / nwork: which units this launch processes, as ranges of a job's
- * pages (KC_WORK_DIGEST) or of its comparison items (KC_WORK_COMPARE,
- * KC_BATCH_ITEM_BYTES of each buffer per item).  NULL = every unit of every
- * job, largest jobs first.  A job may be spread over several launches (a
+ * pages (KC_WORK_DIGEST), of its comparison items (KC_WORK_COMPARE,
+ * KC_BATCH_ITEM_BYTES of each buffer per item) or of its pages to digest
+ * and compare in one pass (KC_WORK_FUSED: a job with both operations; the
+ * comparison of those pages' bytes rides on the digest's read of got, so
+ * got crosses HBM once).  NULL = every unit of every job, largest jobs
+ * first, a job with both operations as one fused range.  A job may be spread over several launches (a
  * serving loop does this); its comparison record is initialised by the
  * launch whose job carries KC_JOB_INIT and accumulates over later launches
  * with order-independent merges, so the result does not depend on how the
@@ -409,6 +412,7 @@ KC_API void kc_va_release(kc_va_lease *lease);
 #define KC_JOB_INIT 0x40
 #define KC_WORK_DIGEST 0
 #define KC_WORK_COMPARE 1
+#define KC_WORK_FUSED 2
 #define KC_BATCH_ITEM_BYTES 65536
 
 typedef struct {
@@ -426,7 +430,7 @@ typedef struct {
 
 typedef struct {
     uint32_t job;          /* index in the job list */
-    uint32_t kind;         /* KC_WORK_DIGEST or KC_WORK_COMPARE */
+    uint32_t kind;         /* KC_WORK_DIGEST, KC_WORK_COMPARE or KC_WORK_FUSED */
     uint64_t first;        /* first unit (page, or comparison item) */
     uint64_t count;        /* number of units */
 } kc_work;

@@ -74,10 +74,12 @@ def make_plan(js, page: int, flags: int = kc.JOB_DIGEST | kc.JOB_COMPARE, device
 
 
 def algorithmic_bytes(plan: Plan) -> int:
-    """Digest reads got once and writes 9 bytes per page; the comparison
-    reads got and want and writes a 64-byte record per job."""
+    """Bytes a digest + compare pass over every job must move: got and want
+    read once each (the fused pass hashes and compares the same read of
+    got), 9 bytes written per page (hash + zero flag) and a 64-byte record
+    per job."""
     n = sum(b for _, b, _ in plan.got)
-    return n + 9 * plan.total_pages + 2 * n + 64 * len(plan.got)
+    return 2 * n + 9 * plan.total_pages + 64 * len(plan.got)
 
 
 def run_batched(ctx: kc.Context, plan: Plan, atol=0.0, rtol=0.0, stream=None) -> int:

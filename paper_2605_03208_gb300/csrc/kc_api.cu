@@ -67,6 +67,7 @@ struct Tables {
     uint64_t items = 0;         // batched form: work items
     int nranges = 0;            // batched form: ranges
     bool any_lost = false;
+    bool fused = false;         // batched form: has fused (digest + compare) ranges
     bool pinned = false;        // read by a captured graph: never recycled
     std::vector<int> buf_status;
     CensusArgs ca{};
@@ -380,8 +381,14 @@ uint32_t *task_counter(kc_ctx *c) { return reinterpret_cast<uint32_t *>(&c->d_mi
 // keep every item resident at once when that fits (up to 24 warps per SM),
 // in CTAs of 2 warps, then give each warp the first ring in the preference
 // list that fits its share of the SM's shared memory.
-DigestShape pick_batch_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
+// Shape of the batched kernel: the forced shape, or enough warps per SM for
+// the tasks and the first ring that fits.  A launch with fused items (got
+// and want chunks in every stage) needs twice the ring; a shape that does
+// not fit a CTA's shared memory loses stages, then halves its chunk (down
+// to 256 bytes), so every forced shape can be launched.
+DigestShape pick_batch_shape(const kc_ctx *c, uint32_t page, uint64_t npages, bool fused) {
     const size_t smem_sm = c->smem_per_sm ? c->smem_per_sm : 228 * 1024;
+    const size_t smem_cta = 227 * 1024;
     DigestShape s = c->forced;
     if (s.lanes == 0) s.lanes = 1;
     const uint64_t ppw = 8ull * (uint64_t)s.lanes;
@@ -393,23 +400,28 @@ DigestShape pick_batch_shape(const kc_ctx *c, uint32_t page, uint64_t npages) {
         if (per_sm > 24) per_sm = 24;
         const uint64_t ctas = (per_sm + s.warps - 1) / s.warps;
         const size_t per_cta = smem_sm / ctas - 1024 - 256;
-        const size_t per_warp = per_cta / s.warps - 128;
         static const int pref[][2] = {{2048, 4}, {2048, 3}, {1024, 2}, {1024, 4}, {1024, 3}, {512, 4},
                                       {512, 3},  {512, 2},  {256, 4},  {256, 3},  {256, 2}};
         s.chunk = 256;
         s.stages = 2;
         for (auto &pc : pref) {
             if ((uint32_t)pc[0] > page) continue;
-            const size_t need = (size_t)pc[1] * ppw * (pc[0] + 32) + pc[1] * 8;
-            if (need <= per_warp) {
-                s.chunk = pc[0];
-                s.stages = pc[1];
+            DigestShape t = s;
+            t.chunk = pc[0];
+            t.stages = pc[1];
+            if (batch_smem_bytes(t, fused) <= per_cta) {
+                s = t;
                 break;
             }
         }
     }
     if ((uint32_t)s.chunk > page) s.chunk = (int)page;
-    const size_t cta_smem = batch_smem_bytes(s);
+    while (batch_smem_bytes(s, fused) > smem_cta) {
+        if (s.stages > 2) --s.stages;
+        else if (s.chunk > 256) s.chunk /= 2;
+        else break;
+    }
+    const size_t cta_smem = batch_smem_bytes(s, fused);
     uint64_t ctas_per_sm = smem_sm / (cta_smem + 1024);
     const uint64_t by_threads = 2048 / (32 * s.warps);
     if (ctas_per_sm > by_threads) ctas_per_sm = by_threads;
@@ -925,8 +937,13 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
                 for (int k = 0; k < njobs; ++k) order[k] = k;
                 std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].bytes > jobs[b].bytes; });
                 for (int k : order) {
-                    if (bj[k].flags & BJ_DIGEST) add((uint32_t)k, 0, 0, pages[k]);
-                    if (bj[k].flags & BJ_COMPARE) add((uint32_t)k, 1, 0, items[k]);
+                    const uint32_t f = bj[k].flags;
+                    if ((f & BJ_DIGEST) && (f & BJ_COMPARE)) {
+                        add((uint32_t)k, BR_FUSED, 0, pages[k]);
+                    } else {
+                        if (f & BJ_DIGEST) add((uint32_t)k, BR_DIGEST, 0, pages[k]);
+                        if (f & BJ_COMPARE) add((uint32_t)k, BR_COMPARE, 0, items[k]);
+                    }
                 }
             } else {
                 for (int w = 0; w < nwork; ++w) {
@@ -939,19 +956,27 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
                     } else if (W.kind == KC_WORK_COMPARE) {
                         if (!(b.flags & BJ_COMPARE) || W.first + W.count > items[W.job] || W.first + W.count < W.first)
                             return fail(c, KC_EINVAL, "work %d: comparison range outside job %u", w, W.job);
+                    } else if (W.kind == KC_WORK_FUSED) {
+                        if (!(b.flags & BJ_DIGEST) || !(b.flags & BJ_COMPARE) || W.first + W.count > pages[W.job] ||
+                            W.first + W.count < W.first)
+                            return fail(c, KC_EINVAL, "work %d: fused range outside job %u (or not both operations)",
+                                        w, W.job);
                     } else {
                         return fail(c, KC_EINVAL, "work %d: kind %u", w, W.kind);
                     }
-                    add(W.job, W.kind == KC_WORK_DIGEST ? 0u : 1u, W.first, W.count);
+                    add(W.job,
+                        W.kind == KC_WORK_DIGEST ? BR_DIGEST : W.kind == KC_WORK_COMPARE ? BR_COMPARE : BR_FUSED,
+                        W.first, W.count);
                 }
             }
             uint64_t it = 0;
             std::vector<uint64_t> per_job(njobs, 0);
             for (auto &r : rg) {
                 r.item_first = it;
-                const uint64_t k = r.kind == 0 ? (r.count + 7) / 8 : r.count;
+                const uint64_t k = r.kind == BR_COMPARE ? r.count : (r.count + 7) / 8;
                 it += k;
                 per_job[r.job] += k;
+                if (r.kind == BR_FUSED) tb.fused = true;
             }
             for (int k = 0; k < njobs; ++k) {
                 if (per_job[k] > 0xFFFFFFFFull) return fail(c, KC_EINVAL, "job %d has more than 2^32 - 1 items", k);
@@ -969,14 +994,14 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
     if (s != KC_OK) return s;
     // digest shape: the persistent grid fills the GPU; warps take digest
     // items and comparison items alike
-    DigestShape shape = pick_batch_shape(c, page_bytes, t->items * 8);
+    DigestShape shape = pick_batch_shape(c, page_bytes, t->items * 8, t->fused);
     shape.lanes = 1;
     shape.ctas = (int)std::min<uint64_t>((uint64_t)shape.ctas, std::max<uint64_t>(1, t->items));
     KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
     {
         Trace tr(c, st);
-        KC_CHECK(c, launch_batch(t->jobs(), njobs, t->left(), t->work(), t->nranges, t->items, page_bytes, shape, atol,
-                                 rtol, task_counter(c), c->sms, st),
+        KC_CHECK(c, launch_batch(t->jobs(), njobs, t->left(), t->work(), t->nranges, t->items, page_bytes, shape,
+                                 t->fused, atol, rtol, task_counter(c), c->sms, st),
                  "batch launch");
     }
     touch(c, t, st);

@@ -104,9 +104,10 @@ struct DigestShape {
 };
 
 // Dynamic shared memory of a CTA of the digest kernel (warps = hash warps)
-// and of the batched kernel (warps = warps of the CTA).
+// and of the batched kernel (warps = warps of the CTA; fused: its stages
+// also hold the compared buffer's chunks).
 size_t digest_smem_bytes(const DigestShape &s);
-size_t batch_smem_bytes(const DigestShape &s);
+size_t batch_smem_bytes(const DigestShape &s, bool fused);
 int digest_max_hash_warps();
 
 // Process-wide count of kernels launched by this library (every launcher
@@ -237,13 +238,17 @@ struct BatchRange {        // 32 bytes
     uint64_t count;        // units
     uint64_t item_first;   // first work item of the range in the launch
     uint32_t job;
-    uint32_t kind;         // 0: digest pages, PPW pages per item; 1: comparison items
+    uint32_t kind;         // BR_DIGEST / BR_COMPARE / BR_FUSED
 };
+// Range kinds: pages to digest (8 per item); comparison items (64 KiB of
+// each buffer per item); pages to digest and compare in one pass (8 per
+// item: got is read once).
+enum : uint32_t { BR_DIGEST = 0, BR_COMPARE = 1, BR_FUSED = 2 };
 constexpr uint32_t BATCH_CMP_ITEM_BYTES = 4 * CMP_TILE_BYTES;   // 64 KiB per comparison item
 static_assert(BATCH_CMP_ITEM_BYTES == KC_BATCH_ITEM_BYTES, "comparison item size");
 cudaError_t launch_batch(const BatchJob *jobs, int njobs, uint32_t *left, const BatchRange *ranges, int nranges,
-                         uint64_t nitems, uint32_t page, const DigestShape &shape, double atol, double rtol,
-                         uint32_t *ctr, int sms, cudaStream_t st);
+                         uint64_t nitems, uint32_t page, const DigestShape &shape, bool fused, double atol,
+                         double rtol, uint32_t *ctr, int sms, cudaStream_t st);
 cudaError_t setup_batch_kernels();
 
 }  // namespace kc

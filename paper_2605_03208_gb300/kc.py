@@ -43,7 +43,7 @@ class KcBuf(ctypes.Structure):
 
 
 JOB_DIGEST, JOB_COMPARE, JOB_INIT = 0x10, 0x20, 0x40
-WORK_DIGEST, WORK_COMPARE = 0, 1
+WORK_DIGEST, WORK_COMPARE, WORK_FUSED = 0, 1, 2
 BATCH_ITEM_BYTES = 65536
 
 

@@ -166,6 +166,53 @@ def test_batch_split_work_over_launches(ctx):
     _check_against_oracle(js, outs, flags)
 
 
+def test_batch_fused_work_over_launches(ctx):
+    """Fused ranges (digest and compare of the same pages in one pass) cut
+    into random pieces over three launches, next to jobs that only digest
+    or only compare: every output equals the oracle's."""
+    js = _small_set(6, n=80)
+    page = 4096
+    outs = Outs(js, page)
+    rng = np.random.default_rng(66)
+    flags = [int(rng.choice([kc.JOB_DIGEST | kc.JOB_COMPARE] * 3 + [kc.JOB_DIGEST, kc.JOB_COMPARE]))
+             for _ in js.sizes]
+    pieces = []
+    for k, b in enumerate(js.sizes):
+        both = flags[k] == kc.JOB_DIGEST | kc.JOB_COMPARE
+        kind = kc.WORK_FUSED if both else kc.WORK_DIGEST if flags[k] == kc.JOB_DIGEST else kc.WORK_COMPARE
+        total = outs.npages[k] if kind != kc.WORK_COMPARE else (b + kc.BATCH_ITEM_BYTES - 1) // kc.BATCH_ITEM_BYTES
+        cuts = sorted(set(rng.integers(0, total + 1, size=int(rng.integers(0, 4))).tolist()) | {0, total})
+        for a, c in zip(cuts[:-1], cuts[1:]):
+            if c > a:
+                pieces.append((k, kind, a, c - a))
+    order = rng.permutation(len(pieces))
+    calls = [[pieces[i] for i in order[j::3]] for j in range(3)]
+    init = [f | kc.JOB_INIT for f in flags]
+    for j, wl in enumerate(calls):
+        jobs = outs.job_dicts(js, init if j == 0 else flags)
+        st = ctx.batch_run(jobs, page, work_array=wl if wl else [(0, kc.WORK_DIGEST, 0, 0)])
+        assert st == kc.OK, ctx.last_error()
+    assert ctx.sync() == kc.OK
+    _check_against_oracle(js, outs, flags)
+
+
+@pytest.mark.parametrize("shape", [(16, 6, 1024), (16, 2, 512), (4, 6, 1024), (8, 3, 256)])
+def test_batch_fused_forced_shapes(ctx, shape):
+    """A forced shape too large for the fused ring (got and want chunks per
+    stage) is shrunk to fit; the results do not depend on the shape."""
+    js = _small_set(7, n=60)
+    page = 65536
+    outs = Outs(js, page)
+    flags = [kc.JOB_DIGEST | kc.JOB_COMPARE] * len(js.sizes)
+    assert ctx.lib.kc_set_digest_shape(ctx.h, *shape, 1) in (kc.OK, kc.EINVAL)
+    try:
+        assert ctx.batch_run(outs.job_dicts(js, flags), page) == kc.OK, ctx.last_error()
+        assert ctx.sync() == kc.OK
+    finally:
+        ctx.set_digest_shape()
+    _check_against_oracle(js, outs, flags)
+
+
 def test_batch_lost_job(ctx):
     js = _small_set(5, n=40)
     page = 65536
@@ -247,6 +294,8 @@ def test_batch_argument_errors(ctx):
     assert bad(lambda j: None, work=[(4, kc.WORK_DIGEST, 0, 1)]) == kc.EINVAL
     assert bad(lambda j: None, work=[(0, 7, 0, 1)]) == kc.EINVAL
     assert bad(lambda j: None, work=[(0, kc.WORK_DIGEST, 0, outs.npages[0] + 1)]) == kc.EINVAL
+    assert bad(lambda j: None, work=[(0, kc.WORK_FUSED, 0, outs.npages[0] + 1)]) == kc.EINVAL
+    assert bad(lambda j: j[1].update(flags=kc.JOB_DIGEST), work=[(1, kc.WORK_FUSED, 0, 1)]) == kc.EINVAL
     assert kc.launch_count() == before
     assert ctx.batch_run(good, 4096) == kc.OK and ctx.sync() == kc.OK
 
