@@ -136,11 +136,12 @@ cudaError_t launch_compare(const CmpPair *pairs, int npairs, const CmpGroups &gr
     for (int d = 0; d < 6 && e == cudaSuccess; ++d) {
         const int n = gr.gfirst[d + 1] - gr.gfirst[d];
         if (n == 0) continue;
-        // two CTAs of 8 warps per SM; small groups use fewer (at least 2048
-        // vectors per warp), and at least one warp per pair
+        // two CTAs of 8 warps per SM; a small group uses fewer, one block of
+        // 32 x CW_U vectors per warp (its time is then about one memory
+        // latency), and at least one warp per pair
         const uint64_t nvec = gr.gvec[d];
         uint64_t blocks = (uint64_t)sms * 2;
-        const uint64_t want = (nvec + 2048ull * CW_WARPS - 1) / (2048ull * CW_WARPS);
+        const uint64_t want = (nvec + 32ull * CW_U * CW_WARPS - 1) / (32ull * CW_U * CW_WARPS);
         const uint64_t least = ((uint64_t)n + CW_WARPS - 1) / CW_WARPS;
         if (want < blocks) blocks = want > least ? want : least;
         if (blocks > (uint64_t)sms * 2) blocks = (uint64_t)sms * 2;

@@ -50,9 +50,9 @@ def run_digest(ctx, snap, dev, page_bytes=None, flags=None):
     return st, to_np(h)[:P].view(np.uint64), to_np(z)[:P], to_np(pf).view(np.uint64)
 
 
-def run_scan(ctx, snap, dev, win, cap=None, page_bytes=None):
+def run_scan(ctx, snap, dev, win, cap=None, page_bytes=None, flags=None):
     S = page_bytes or snap.page_bytes
-    b = region_bufs(snap, dev)
+    b = region_bufs(snap, dev, flags)
     P = kc.page_count(b, S)
     if cap is None:
         cap = sum(int(s) // 8 for s in snap.sizes)

@@ -155,6 +155,66 @@ def test_scan_dense_pointers_many_chunks(ctx, page):
     assert ctx.sync() == kc.OK and (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
 
 
+def _sparse_pointer_fill(snap, bases, seed=0, n_ptr=1000):
+    """Random bytes with n_ptr pointer words planted at random 8-byte
+    offsets, plus an inside pointer in every word of each region's end past
+    its last full 32-byte stripe."""
+    rng = np.random.default_rng(seed + 5)
+    snap.bases = [int(b) for b in bases]
+    regions = [rng.integers(0, 256, s, dtype=np.uint8) for s in snap.sizes]
+    weight = np.array(snap.sizes, dtype=np.float64) / sum(snap.sizes)
+    for _ in range(n_ptr):
+        i = int(rng.choice(len(snap.sizes), p=weight))
+        w = int(rng.integers(0, snap.sizes[i] // 8))
+        if rng.random() < 0.1:
+            v = W._outside_value(rng, snap.bases, snap.sizes)
+        else:
+            v, _ = W._inside_value(rng, snap.bases, snap.sizes)
+        regions[i][8 * w:8 * w + 8] = np.array([v], np.uint64).view(np.uint8)
+    for i, s in enumerate(snap.sizes):
+        for o in range(s & ~31, s - 7, 8):
+            v, _ = W._inside_value(rng, snap.bases, snap.sizes)
+            regions[i][o:o + 8] = np.array([v], np.uint64).view(np.uint8)
+    snap.regions = regions
+    snap.truth = {}
+    return snap
+
+
+@pytest.mark.parametrize("page", [4096, 2 * W.MiB])
+@pytest.mark.parametrize("n_ptr", [300, 3000, 6000])
+def test_scan_sparse_pointers(ctx, page, n_ptr):
+    """Sparse pointers (300 to 6000 among random bytes) at 4 KiB and 2 MiB
+    pages: hits in the regions' last words (past the last full 32-byte
+    stripe, hashed from global memory), truncation, counts only and a lost
+    region, all as the oracle's."""
+    MiB = W.MiB
+    sizes = [MiB + 24, 3 * MiB + 8, 517 * 4096 + 16, 64 * 1024 + 8, 40]
+    layout = W.Snapshot("census-log", page, sizes, dtypes=[kc.RAW] * len(sizes))
+    snap, dev = G.device_snapshot(layout, _sparse_pointer_fill, 11, n_ptr=n_ptr)
+    win = W.default_window(snap.bases, snap.sizes)
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert rc == 0 and nin + nout >= n_ptr * 0.9
+    oh, oz, _ = _oracle_digest(snap, page)
+    st, r = G.run_scan(ctx, snap, dev, win, page_bytes=page)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][: nin + nout]) == G.hits_tuples(ohits)
+    assert np.array_equal(r["hash"], oh) and np.array_equal(r["zero"], oz)
+    st, r = G.run_scan(ctx, snap, dev, win, cap=100, page_bytes=page)
+    assert ctx.sync() == kc.ETRUNC
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][:100]) == G.hits_tuples(ohits[:100])
+    st, r = G.run_scan(ctx, snap, dev, win, cap=0, page_bytes=page)
+    assert ctx.sync() == kc.OK and (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    # region 1 lost: not scanned, still a target
+    flags = [0, kc.BUF_LOST, 0, 0, 0]
+    st, r = G.run_scan(ctx, snap, dev, win, page_bytes=page, flags=flags)
+    assert st == kc.EBUF and ctx.sync() == kc.OK
+    keep = [x for x in G.hits_tuples(ohits) if x[0] != 1]
+    assert G.hits_tuples(r["hits"][: len(keep)]) == keep
+    assert int(r["counts"][0]) + int(r["counts"][1]) == len(keep)
+
+
 def test_scan_page_mode_above_list_limit(ctx):
     """More than 65536 pages: the fused scan's census tail takes chunks of
     consecutive pages (page mode) instead of the list of flagged pages; hits,
