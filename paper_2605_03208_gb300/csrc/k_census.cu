@@ -202,12 +202,14 @@ __device__ __forceinline__ void tail_run(const Pages &u, const CensusArgs &ca, c
 }
 
 // The flagged pages (page_hits != 0) in page order, for the tail's list
-// mode: one CTA, a block-wide scan per tile of pages.
+// mode: one CTA, a block-wide scan per tile of pages; an entry is the page
+// << 32 | its mark (region + 1), so the tail needs no second look-up.
 constexpr int FLAG_THREADS = 1024;
 constexpr int FLAG_ITEMS = 8;
 
 __global__ void __launch_bounds__(FLAG_THREADS) census_flag_list_kernel(const uint32_t *__restrict__ page_hits,
-                                                                        uint64_t npages, uint32_t *__restrict__ list,
+                                                                        uint64_t npages,
+                                                                        unsigned long long *__restrict__ list,
                                                                         uint32_t *__restrict__ nlist) {
     __shared__ uint32_t ws[32];
     __shared__ uint32_t s_base;
@@ -216,10 +218,12 @@ __global__ void __launch_bounds__(FLAG_THREADS) census_flag_list_kernel(const ui
     __syncthreads();
     for (uint64_t t0 = 0; t0 < npages; t0 += (uint64_t)FLAG_THREADS * FLAG_ITEMS) {
         uint32_t f = 0, n = 0;
+        uint32_t mark[FLAG_ITEMS];
 #pragma unroll
         for (int j = 0; j < FLAG_ITEMS; ++j) {
             const uint64_t p = t0 + (uint64_t)tid * FLAG_ITEMS + j;
-            const bool on = p < npages && page_hits[p] != 0;
+            mark[j] = p < npages ? page_hits[p] : 0u;
+            const bool on = mark[j] != 0;
             f |= (uint32_t)on << j;
             n += on;
         }
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(FLAG_THREADS) census_flag_list_kernel(const ui
         uint32_t at = s_base + ws[warp] + inc - n;
 #pragma unroll
         for (int j = 0; j < FLAG_ITEMS; ++j)
-            if ((f >> j) & 1) list[at++] = (uint32_t)(t0 + (uint64_t)tid * FLAG_ITEMS + j);
+            if ((f >> j) & 1) list[at++] = ((t0 + (uint64_t)tid * FLAG_ITEMS + j) << 32) | mark[j];
         __syncthreads();
         if (tid == FLAG_THREADS - 1) s_base = at;
         __syncthreads();
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
                                                                     const uint32_t *__restrict__ page_hits,
                                                                     unsigned long long *__restrict__ tail,
                                                                     uint64_t nchunks, uint32_t cpages,
-                                                                    const uint32_t *__restrict__ list,
+                                                                    const unsigned long long *__restrict__ list,
                                                                     const uint32_t *__restrict__ nlist,
                                                                     kc_hit *__restrict__ hits, uint64_t cap,
                                                                     uint64_t *__restrict__ counts,
@@ -274,28 +278,38 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
     __shared__ uint32_t wn[TAIL_WARPS], win_s[TAIL_WARPS], wout_s[TAIL_WARPS];
     __shared__ int s_nflag;
     __shared__ unsigned long long s_chunk, s_prefix;
-    const Range *rg = stage_ranges(ca, srg);
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     unsigned long long *ticket = tail;
     volatile unsigned long long *word = tail + 1;
+    // the first ticket and the list length are fetched while the ranges are staged
+    if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1ull);
     const uint64_t nentries = list ? (uint64_t)*nlist : u.npages;
+    const Range *rg = stage_ranges(ca, srg);
+    __syncthreads();   // (stage_ranges has none when the ranges stay in global memory)
     if (list) {   // spread the flagged pages over the grid: at most TAIL_CHUNK per chunk
         uint64_t cp = (nentries + gridDim.x - 1) / gridDim.x;
         cpages = (uint32_t)(cp < 1 ? 1 : cp > (uint64_t)TAIL_CHUNK ? TAIL_CHUNK : cp);
         nchunks = (nentries + cpages - 1) / cpages;
     }
-    while (true) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1ull);
-        __syncthreads();
+    // with no more chunks than CTAs, every CTA takes exactly one ticket, so the
+    // tickets 0 .. gridDim.x - 1 cover every chunk and none takes a second
+    const bool one_round = nchunks <= gridDim.x;
+    for (bool first = true;; first = false) {
+        if (!first) {
+            if (one_round) break;
+            if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1ull);
+            __syncthreads();
+        }
         const uint64_t c = s_chunk;
         if (c >= nchunks) break;
         const uint64_t e0 = c * cpages;
         const uint64_t e1 = e0 + cpages < nentries ? e0 + cpages : nentries;
         if (warp == 0) {   // the flagged pages and their word offsets in the chunk's sequence
             const uint64_t e = e0 + lane;
-            const uint64_t p = e < e1 ? (list ? (uint64_t)list[e] : e) : 0;
-            const uint32_t r = e < e1 ? page_hits[p] : 0u;
+            const unsigned long long ent = (list && e < e1) ? list[e] : 0ull;
+            const uint64_t p = e < e1 ? (list ? ent >> 32 : e) : 0;
+            const uint32_t r = e < e1 ? (list ? (uint32_t)ent : page_hits[p]) : 0u;
             const uint64_t nw = r ? page_span(u, p, (int)r - 1).nwords : 0;
             const uint32_t fm = __ballot_sync(0xffffffffu, r != 0);
             uint64_t inc = nw;
@@ -402,13 +416,13 @@ uint64_t census_tail_words(uint64_t npages, int sms) {
 }
 
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
-                               uint32_t *list, kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status,
-                               int sms, uint32_t spin_limit, cudaStream_t st) {
+                               unsigned long long *list, kc_hit *hits, uint64_t cap, uint64_t *counts,
+                               uint32_t *status, int sms, uint32_t spin_limit, cudaStream_t st) {
     if (pg.npages == 0) return cudaSuccess;
     if (spin_limit == 0) spin_limit = LB_SPIN_LIMIT;
     const uint64_t maxb = (uint64_t)sms * 2;
     if (pg.npages <= TAIL_LIST_MAX) {
-        uint32_t *nlist = list + pg.npages;
+        uint32_t *nlist = reinterpret_cast<uint32_t *>(list + pg.npages);
         census_flag_list_kernel<<<1, FLAG_THREADS, 0, st>>>(page_hits, pg.npages, list, nlist);
         count_launches(1);
         cudaError_t e = cudaGetLastError();
