@@ -205,6 +205,10 @@ KC_API kc_status kc_set_trace_events(kc_ctx *ctx, void *start, void *stop);
 KC_API uint64_t kc_page_count(const kc_buf *bufs, int n, uint32_t page_bytes);
 
 /* ---- digest ---------------------------------------------------------------
+ * Defined by: Section "Memory Capture" (HIP path), which snapshots every
+ * tracked region verbatim at its VA; the per-page XXH64 digest is this
+ * library's reduction of that snapshot on the device (the paper hashes only
+ * code objects), so that equal pages can be found and stored once.
  * For region i (list order) and page j = 0 .. ceil(bytes_i / S) - 1:
  *   d_hash[p] = XXH64(seed 0) of bytes [jS, min((j+1)S, bytes_i)), unpadded;
  *   d_zero[p] = KC_PAGE_ZERO if every one of those bytes is 0, else
@@ -218,6 +222,11 @@ KC_API kc_status kc_digest(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t pa
                     uint64_t *d_hash, uint8_t *d_zero, uint64_t *d_page_first, void *stream);
 
 /* ---- census ---------------------------------------------------------------
+ * Defined by: Section "Memory Capture", paragraphs "Handling embedded device
+ * pointers via address-space closure" and its bounds -- the snapshot stays
+ * valid only if the pointers it embeds point into captured regions; the
+ * census counts and lists the words that do (inside) and the words that
+ * point elsewhere in the device VA window (outside).
  * For every region i (list order) and every offset o = 0, 8, ... with
  * o + 8 <= bytes_i, the little-endian u64 word v at base_i + o is
  *   INSIDE  (target k) if base_k <= v < base_k + bytes_k for some region k,
@@ -268,7 +277,9 @@ KC_API kc_status kc_census(kc_ctx *ctx, const kc_buf *allocs, int n, uint64_t wi
 KC_API kc_status kc_census_static(const kc_buf *allocs, int n, uint64_t win_lo, uint64_t win_hi,
                                   kc_hit *d_hits, uint64_t cap, uint64_t *d_counts, void *stream);
 
-/* kc_scan: kc_digest and kc_census fused into one read of the snapshot
+/* kc_scan (Sections "Memory Capture" and its address-space closure
+ * paragraphs, as kc_digest and kc_census): kc_digest and kc_census fused
+ * into one read of the snapshot
  * (while pages are hashed, a conservative test on the high 32 bits of every
  * word flags the pages that may hold hits; only those are read a second
  * time, classified and written in order).  Outputs and errors
@@ -279,6 +290,10 @@ KC_API kc_status kc_scan(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t page
                   uint64_t *d_counts, void *stream);
 
 /* ---- dedup ----------------------------------------------------------------
+ * Defined by: Section "Memory Capture" (the verbatim snapshot the paper
+ * writes per region); storing each distinct page once, with a table that
+ * rebuilds every region, is this library's device-side reduction of it and
+ * loses no byte (byte equality decides, below).
  * Input: the digest of the same regions at the same page size (d_hash,
  * d_zero).  Non-zero pages are grouped by their hashes (a device radix sort;
  * up to 8192 pages, shared-memory hash tables) and byte-verified; the
@@ -297,6 +312,8 @@ KC_API kc_status kc_dedup(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t pag
                    uint8_t *d_arena, uint64_t arena_cap, uint64_t *d_n_blobs, void *stream);
 
 /* ---- restore --------------------------------------------------------------
+ * Defined by: Section "VA-Faithful HSA Replay", stage 5 (the captured data
+ * is copied back at the VAs it was captured at, so embedded pointers hold).
  * For each of the n_pages rows r of d_table: len = min(S, bytes_a - off)
  * with a = r.alloc_id, off = r.va_offset; write len bytes at base_a + off:
  * zeros for KC_BLOB_ZERO, nothing for KC_BLOB_LOST, else the bytes
@@ -314,6 +331,9 @@ KC_API kc_status kc_restore(kc_ctx *ctx, const kc_buf *allocs, int n, uint32_t p
                      uint64_t arena_bytes, void *stream);
 
 /* ---- compare --------------------------------------------------------------
+ * Defined by: Section "Replay Validation" (replayed outputs are checked
+ * against the captured ones byte for byte, or with numpy.allclose-style
+ * tolerances, NaNs reported explicitly).
  * For pair k, got[k] and want[k] hold the same number of bytes, a multiple
  * of the element size of got[k].dtype (want[k].dtype is ignored).  Every
  * element is widened exactly to FP64 (a = got, b = want):
