@@ -512,10 +512,12 @@ __device__ __forceinline__ void vec_found(const uint4 &g, const uint4 &w, unsign
     const uint32_t FULL = 0xffffffffu;
     float ma = 0.0f, mr = 0.0f;
     if (differs) vec_classify<DT>(g, w, v, acc, ma, mr);
+    // usually no lane's proxies reach the threshold: one vote, no reductions
+    const bool beat = ma > 0.0f && (!(ma < q.run_abs * PROXY_KEEP) || !(mr < q.run_rel * PROXY_KEEP));
+    if (!__any_sync(FULL, beat)) return;
     // proxies are >= 0 (or +inf), so their bit patterns order like their values
     const float wa = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(ma)));
     const float wr = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mr)));
-    if (!(wa > 0.0f) || (wa < q.run_abs * PROXY_KEEP && wr < q.run_rel * PROXY_KEEP)) return;
     float ra = fmaxf(q.run_abs, wa), rr = fmaxf(q.run_rel, wr);
     if (q.gate) {
         uint32_t ga = 0u, gr = 0u;
