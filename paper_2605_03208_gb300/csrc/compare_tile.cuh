@@ -264,16 +264,16 @@ __device__ __forceinline__ void cmp_drain_any(int dt, const SlowQ &q, uint32_t m
 
 // ---- warp-streaming comparison -------------------------------------------------
 //
-// A warp streams its own contiguous range of 16-byte vectors of a pair (no
-// block barriers).  A vector whose bits differ anywhere is rare; the lane
-// that finds one does not evaluate it there (the other 31 lanes would idle
-// through the per-element work) but appends the whole vector to the warp's
-// queue in shared memory (one ballot per load, its slot from a popcount);
-// the warp evaluates queued vectors 32 at a time, one per lane, with every
-// lane busy -- NaNs of the vector's equal elements counted, its differing
-// elements widened to FP64 -- when the queue would overflow and when the
-// warp's part of the pair ends.  Equal vectors only have their NaNs counted
-// (two bit tricks per word).
+// A warp streams blocks of 16-byte vectors of a pair (no block barriers;
+// the kernel decides which blocks, k_compare.cu).  Equal vectors only have
+// their NaNs counted (two bit tricks per word).  A vector whose bits differ
+// is rare: with zero tolerances the lane that finds it classifies it where
+// it is and FP64 runs only for the few elements that can hold the maxima
+// (below); with tolerances every differing element needs FP64, so the
+// vector goes to the warp's queue in shared memory (one ballot per load, its
+// slot from a popcount) and the warp evaluates queued vectors 32 at a time,
+// one per lane, with every lane busy, when the queue would overflow and
+// when it leaves the pair.
 
 __device__ __forceinline__ CmpAcc cmp_acc_zero() { return CmpAcc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0}; }
 
