@@ -267,13 +267,12 @@ __device__ __forceinline__ void cmp_drain_any(int dt, const SlowQ &q, uint32_t m
 // A warp streams blocks of 16-byte vectors of a pair (no block barriers;
 // the kernel decides which blocks, k_compare.cu).  Equal vectors only have
 // their NaNs counted (two bit tricks per word).  A vector whose bits differ
-// is rare: with zero tolerances the lane that finds it classifies it where
-// it is and FP64 runs only for the few elements that can hold the maxima
-// (below); with tolerances every differing element needs FP64, so the
-// vector goes to the warp's queue in shared memory (one ballot per load, its
-// slot from a popcount) and the warp evaluates queued vectors 32 at a time,
-// one per lane, with every lane busy, when the queue would overflow and
-// when it leaves the pair.
+// is rare: it goes to the warp's queue in shared memory (one ballot per
+// load, its slot from a popcount), and the warp evaluates queued vectors 32
+// at a time, one per lane, with every lane busy, when the queue would
+// overflow and when it leaves the pair.  With tolerances every differing
+// element is evaluated in FP64; with zero tolerances FP64 runs only for the
+// few elements that can hold the maxima (below).
 
 __device__ __forceinline__ CmpAcc cmp_acc_zero() { return CmpAcc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0}; }
 
@@ -425,23 +424,20 @@ __device__ __forceinline__ void cmp_acc_merge(CmpAcc &a, const CmpAcc &b) {
     a.max_rel = b.max_rel > a.max_rel ? b.max_rel : a.max_rel;
 }
 
-template <int DT>
-__device__ __forceinline__ void wq_drain(WarpQ &q, double atol, double rtol, CmpAcc &acc) {
-    if (q.n == 0) return;
-    cmp_acc_merge(acc, wq_eval<DT>(q.items, q.n, atol, rtol));
-    q.n = 0;
-}
 
-// ---- zero tolerances: differing vectors handled where they are found ---------
+// ---- zero tolerances: queued differing vectors, classified in batches -------
 //
 // With atol == rtol == 0 an unequal element is a mismatch from its bits
-// alone, so a lane classifies the elements of its differing vector at once
-// (counts, first index, NaN rules) and takes the largest proxies.  Only when
-// the warp's largest proxy reaches its running threshold (the warp's and the
-// pair's gate maxima times 1 - 2^-18) does the warp publish it to the gate,
-// refresh the threshold from it and evaluate the elements still above it in
-// FP64.  Such records are few (a running maximum over the pair), so FP64
-// work is spread thinly over the kernel instead of being queued to its end.
+// alone.  Differing vectors are queued per warp (as with tolerances) and
+// evaluated 32 at a time, one per lane: each lane classifies its vector's
+// elements (counts, first index, NaN rules) and takes the largest proxies;
+// only when some lane's proxy reaches the warp's running threshold (the
+// warp's and the pair's gate maxima times 1 - 2^-18) does the warp reduce
+// the proxies, publish them to the gate, refresh the threshold and evaluate
+// the elements still above it in FP64.  Such records are few (a running
+// maximum over the pair).  (Classifying each differing vector where it was
+// found instead cost its warp that latency in the middle of the stream:
+// flipped MoE pair 33.3 against 29.4 us, 300k flips 85 against 48 us.)
 
 // Lane-local pass over one differing vector: everything but the FP64
 // maxima; ma / mr receive the largest proxies of its unequal numbers.
@@ -502,42 +498,65 @@ __device__ __forceinline__ void vec_exact_max(const uint4 &g, const uint4 &w, fl
     }
 }
 
-// A warp step with at least one differing vector (zero tolerances); all
-// lanes call it.  The warp's running proxy maxima live in q; the pair's gate
-// is read with a plain load and raised (atomic max, no return) only by a
-// warp holding a larger maximum, so warps do not queue on one address.
+// Zero tolerances: n queued vectors, 32 at a time with every lane busy --
+// classified (vec_classify), then, only where a lane's proxy reaches the
+// threshold, the warp maxima, the pair's gate and FP64.
+// run: the warp's running proxy maxima, updated.
 template <int DT>
-__device__ __forceinline__ void vec_found(const uint4 &g, const uint4 &w, unsigned long long v, bool differs,
-                                          WarpQ &q, CmpAcc &acc) {
+__device__ __noinline__ CmpAcc wq_eval_zt(const VecItem *items, uint32_t n, float *run, uint32_t *gate) {
     const uint32_t FULL = 0xffffffffu;
-    float ma = 0.0f, mr = 0.0f;
-    if (differs) vec_classify<DT>(g, w, v, acc, ma, mr);
-    // usually no lane's proxies reach the threshold: one vote, no reductions
-    const bool beat = ma > 0.0f && (!(ma < q.run_abs * PROXY_KEEP) || !(mr < q.run_rel * PROXY_KEEP));
-    if (!__any_sync(FULL, beat)) return;
-    // proxies are >= 0 (or +inf), so their bit patterns order like their values
-    const float wa = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(ma)));
-    const float wr = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mr)));
-    float ra = fmaxf(q.run_abs, wa), rr = fmaxf(q.run_rel, wr);
-    if (q.gate) {
-        uint32_t ga = 0u, gr = 0u;
-        if (lane_id() == 0) {
-            ga = *reinterpret_cast<volatile uint32_t *>(q.gate);
-            gr = *reinterpret_cast<volatile uint32_t *>(q.gate + 1);
-            if (__float_as_uint(ra) > ga) atomicMax(q.gate, __float_as_uint(ra));
-            if (__float_as_uint(rr) > gr) atomicMax(q.gate + 1, __float_as_uint(rr));
+    CmpAcc a = cmp_acc_zero();
+    float ra = run[0], rr = run[1];
+    __syncwarp();
+    for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+        const uint32_t i = b0 + lane_id();
+        const bool have = i < n;
+        VecItem it{0ull, make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        float ma = 0.0f, mr = 0.0f;
+        if (have) {
+            it = items[i];
+            vec_classify<DT>(it.g, it.w, it.v, a, ma, mr);
         }
-        ra = fmaxf(ra, __uint_as_float(__shfl_sync(FULL, ga, 0)));
-        rr = fmaxf(rr, __uint_as_float(__shfl_sync(FULL, gr, 0)));
+        const bool beat = ma > 0.0f && (!(ma < ra * PROXY_KEEP) || !(mr < rr * PROXY_KEEP));
+        if (!__any_sync(FULL, beat)) continue;
+        ra = fmaxf(ra, __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(ma))));
+        rr = fmaxf(rr, __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mr))));
+        if (gate) {
+            uint32_t ga = 0u, gr = 0u;
+            if (lane_id() == 0) {
+                ga = *reinterpret_cast<volatile uint32_t *>(gate);
+                gr = *reinterpret_cast<volatile uint32_t *>(gate + 1);
+                if (__float_as_uint(ra) > ga) atomicMax(gate, __float_as_uint(ra));
+                if (__float_as_uint(rr) > gr) atomicMax(gate + 1, __float_as_uint(rr));
+            }
+            ra = fmaxf(ra, __uint_as_float(__shfl_sync(FULL, ga, 0)));
+            rr = fmaxf(rr, __uint_as_float(__shfl_sync(FULL, gr, 0)));
+        }
+        if (have) vec_exact_max<DT>(it.g, it.w, ra * PROXY_KEEP, rr * PROXY_KEEP, a);
     }
-    if (differs) vec_exact_max<DT>(g, w, ra * PROXY_KEEP, rr * PROXY_KEEP, acc);
-    q.run_abs = ra;
-    q.run_rel = rr;
+    __syncwarp();
+    run[0] = ra;
+    run[1] = rr;
+    return a;
+}
+
+template <int DT, bool ZT>
+__device__ __forceinline__ void wq_drain(WarpQ &q, double atol, double rtol, CmpAcc &acc) {
+    if (q.n == 0) return;
+    if (ZT) {
+        float run[2] = {q.run_abs, q.run_rel};
+        cmp_acc_merge(acc, wq_eval_zt<DT>(q.items, q.n, run, q.gate));
+        q.run_abs = run[0];
+        q.run_rel = run[1];
+    } else {
+        cmp_acc_merge(acc, wq_eval<DT>(q.items, q.n, atol, rtol));
+    }
+    q.n = 0;
 }
 
 // One vector per lane (vector index v, `differs` when its bits differ):
-// NaNs of equal vectors are counted; differing ones are handled at once
-// (ZT: zero tolerances) or queued.  All lanes call it.
+// NaNs of equal vectors are counted; differing ones are queued (evaluated
+// by wq_eval_zt with zero tolerances, ZT, else by wq_eval).  All lanes call it.
 template <int DT, bool ZT>
 __device__ __forceinline__ void vec_step(WarpQ &q, const uint4 &g, const uint4 &w, unsigned long long v,
                                          bool valid, double atol, double rtol, CmpAcc &acc) {
@@ -549,11 +568,7 @@ __device__ __forceinline__ void vec_step(WarpQ &q, const uint4 &g, const uint4 &
     }
     const uint32_t b = __ballot_sync(0xffffffffu, differs);
     if (b == 0u) return;
-    if (ZT) {
-        vec_found<DT>(g, w, v, differs, q, acc);
-        return;
-    }
-    if (q.n + 32 > q.cap) wq_drain<DT>(q, atol, rtol, acc);
+    if (q.n + 32 > q.cap) wq_drain<DT, ZT>(q, atol, rtol, acc);
     if (differs) q.items[q.n + __popc(b & lanemask_lt())] = VecItem{v, g, w};
     q.n += __popc(b);
 }
@@ -588,18 +603,14 @@ __device__ __forceinline__ void warp_compare_range(const CmpPair &pr, uint64_t v
                 dm |= (uint32_t)d << u;
             }
             if (__any_sync(0xffffffffu, dm != 0u)) {
-#pragma unroll 1
+#pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const bool d = (dm >> u) & 1u;
-                    if (!__any_sync(0xffffffffu, d)) continue;
-                    uint4 gs = gv[0], ws = wv[0];
-#pragma unroll
-                    for (int t = 1; t < U; ++t)
-                        if (u == t) {
-                            gs = gv[t];
-                            ws = wv[t];
-                        }
-                    vec_found<DT>(gs, ws, v + 32 * u + lane, d, q, acc);
+                    const uint32_t b = __ballot_sync(0xffffffffu, d);
+                    if (b == 0u) continue;
+                    if (q.n + 32 > q.cap) wq_drain<DT, true>(q, atol, rtol, acc);
+                    if (d) q.items[q.n + __popc(b & lanemask_lt())] = VecItem{v + 32 * u + lane, gv[u], wv[u]};
+                    q.n += __popc(b);
                 }
             }
         } else {

@@ -31,7 +31,7 @@ namespace kc {
 constexpr int CW_WARPS = 8;
 constexpr int CW_THREADS = 32 * CW_WARPS;
 constexpr int CW_U = 4;
-constexpr uint32_t CW_QCAP = 128;   // queued vectors per warp (40 B each)
+constexpr uint32_t CW_QCAP = 128;   // queued vectors per warp (40 B each; both tolerance modes)
 
 template <int DT, bool ZT>
 __global__ void __launch_bounds__(CW_THREADS, 2) cmp_kernel(const CmpPair *__restrict__ pairs, int npairs, uint64_t nvec,
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(CW_THREADS, 2) cmp_kernel(const CmpPair *__res
         while (v < b1) {
             if (k < 0 || v >= pend) {
                 if (k >= 0) {
-                    wq_drain<DT>(q, atol, rtol, acc);
+                    wq_drain<DT, ZT>(q, atol, rtol, acc);
                     cmp_warp_flush(acc, &out[pr.out_index]);
                     acc = cmp_acc_zero();
                 }
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(CW_THREADS, 2) cmp_kernel(const CmpPair *__res
         }
     }
     if (k >= 0) {
-        wq_drain<DT>(q, atol, rtol, acc);
+        wq_drain<DT, ZT>(q, atol, rtol, acc);
         cmp_warp_flush(acc, &out[pr.out_index]);
     }
     for (uint64_t t = wid; t < (uint64_t)npairs; t += nw) {
@@ -104,7 +104,7 @@ __global__ void cmp_init_kernel(const CmpPair *__restrict__ pairs, int npairs, k
     gates[2 * (uint64_t)o + 1] = 0u;
 }
 
-constexpr size_t CW_SMEM = (size_t)CW_WARPS * CW_QCAP * sizeof(VecItem);   // the queues (tolerance kernels)
+constexpr size_t CW_SMEM = (size_t)CW_WARPS * CW_QCAP * sizeof(VecItem);   // the warps' queues
 
 template <int DT>
 cudaError_t setup_cmp_dtype() {
@@ -124,7 +124,7 @@ template <int DT>
 void launch_cmp_dtype(dim3 g, const CmpPair *gp, int n, uint64_t nvec, double atol, double rtol, kc_cmp_result *out,
                       uint32_t *gates, cudaStream_t st) {
     const dim3 b(CW_THREADS);
-    if (atol == 0.0 && rtol == 0.0) cmp_kernel<DT, true><<<g, b, 0, st>>>(gp, n, nvec, atol, rtol, out, gates);
+    if (atol == 0.0 && rtol == 0.0) cmp_kernel<DT, true><<<g, b, CW_SMEM, st>>>(gp, n, nvec, atol, rtol, out, gates);
     else cmp_kernel<DT, false><<<g, b, CW_SMEM, st>>>(gp, n, nvec, atol, rtol, out, gates);
 }
 
