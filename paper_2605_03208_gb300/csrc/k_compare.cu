@@ -31,7 +31,7 @@ namespace kc {
 constexpr int CW_WARPS = 8;
 constexpr int CW_THREADS = 32 * CW_WARPS;
 constexpr int CW_U = 4;
-constexpr uint32_t CW_QCAP = 128;   // queued vectors per warp (40 B each; both tolerance modes)
+constexpr uint32_t CW_QCAP = 128;   // queued vectors per warp (48 B each; both tolerance modes)
 
 template <int DT, bool ZT>
 __global__ void __launch_bounds__(CW_THREADS, 2) cmp_kernel(const CmpPair *__restrict__ pairs, int npairs, uint64_t nvec,
@@ -108,7 +108,10 @@ constexpr size_t CW_SMEM = (size_t)CW_WARPS * CW_QCAP * sizeof(VecItem);   // th
 
 template <int DT>
 cudaError_t setup_cmp_dtype() {
-    return cudaFuncSetAttribute(cmp_kernel<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CW_SMEM);
+    const cudaError_t e =
+        cudaFuncSetAttribute(cmp_kernel<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CW_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(cmp_kernel<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CW_SMEM);
 }
 
 cudaError_t setup_compare_kernels() {
