@@ -136,8 +136,11 @@ typedef struct kc_ctx kc_ctx;
  * kc_create: make a context on CUDA device `device`.  The context owns
  * device scratch (sort buffers, counters, region tables) that grows on
  * demand; growth is refused inside a stream capture (KC_ENOMEM), so make one
- * uncaptured call of each shape first.  Returns KC_OK, KC_EINVAL (null out,
- * bad device) or KC_ECUDA.
+ * uncaptured call of each shape first.  Calls on one context share that
+ * scratch (and the task counter of the digest), so they must be ordered on
+ * the device: one stream per context, or streams the caller orders with
+ * events; for work that should overlap, use one context per stream.
+ * Returns KC_OK, KC_EINVAL (null out, bad device) or KC_ECUDA.
  * kc_destroy: release everything (waits for the context's work to finish).
  * kc_last_error: human-readable reason of the last failing call (owned by
  * the context, valid until the next call).
