@@ -201,71 +201,18 @@ __device__ __forceinline__ void tail_run(const Pages &u, const CensusArgs &ca, c
     }
 }
 
-// The flagged pages (page_hits != 0) in page order, for the tail's list
-// mode: one CTA, a block-wide scan per tile of pages; an entry is the page
-// << 32 | its mark (region + 1), so the tail needs no second look-up.
-constexpr int FLAG_THREADS = 1024;
-constexpr int FLAG_ITEMS = 8;
-
-__global__ void __launch_bounds__(FLAG_THREADS) census_flag_list_kernel(const uint32_t *__restrict__ page_hits,
-                                                                        uint64_t npages,
-                                                                        unsigned long long *__restrict__ list,
-                                                                        uint32_t *__restrict__ nlist) {
-    __shared__ uint32_t ws[32];
-    __shared__ uint32_t s_base;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_base = 0;
-    __syncthreads();
-    for (uint64_t t0 = 0; t0 < npages; t0 += (uint64_t)FLAG_THREADS * FLAG_ITEMS) {
-        uint32_t f = 0, n = 0;
-        uint32_t mark[FLAG_ITEMS];
-#pragma unroll
-        for (int j = 0; j < FLAG_ITEMS; ++j) {
-            const uint64_t p = t0 + (uint64_t)tid * FLAG_ITEMS + j;
-            mark[j] = p < npages ? page_hits[p] : 0u;
-            const bool on = mark[j] != 0;
-            f |= (uint32_t)on << j;
-            n += on;
-        }
-        uint32_t inc = n;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) ws[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t x = ws[lane];
-            uint32_t xi = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, o);
-                if (lane >= o) xi += y;
-            }
-            ws[lane] = xi - x;
-        }
-        __syncthreads();
-        uint32_t at = s_base + ws[warp] + inc - n;
-#pragma unroll
-        for (int j = 0; j < FLAG_ITEMS; ++j)
-            if ((f >> j) & 1) list[at++] = ((t0 + (uint64_t)tid * FLAG_ITEMS + j) << 32) | mark[j];
-        __syncthreads();
-        if (tid == FLAG_THREADS - 1) s_base = at;
-        __syncthreads();
-    }
-    if (tid == 0) *nlist = s_base;
-}
-
-// List mode (list != null): chunk c holds entries [c * cpages, ...) of the
-// page-ordered list of flagged pages (*nlist of them), so a chunk's work is
-// bounded by cpages pages however the flagged pages cluster.
+// List mode (snapshots up to TAIL_LIST_MAX pages): every CTA reads the
+// digest's page marks itself -- thread i a run of G consecutive pages, G the
+// pages per thread rounded up to 4 (at most 128), kept as bits -- and a
+// block-wide scan of the bit counts numbers the flagged pages (mark != 0) in
+// page order.  Chunk c holds flagged pages [c * cpages, ...), so a chunk's
+// work is bounded by cpages pages however the flagged pages cluster, and
+// each CTA finds its chunk's pages from the scan, with no list kernel.
 __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, CensusArgs ca,
                                                                     const uint32_t *__restrict__ page_hits,
                                                                     unsigned long long *__restrict__ tail,
                                                                     uint64_t nchunks, uint32_t cpages,
-                                                                    const unsigned long long *__restrict__ list,
-                                                                    const uint32_t *__restrict__ nlist,
+                                                                    bool list,
                                                                     kc_hit *__restrict__ hits, uint64_t cap,
                                                                     uint64_t *__restrict__ counts,
                                                                     uint32_t *__restrict__ status,
@@ -278,15 +225,56 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
     __shared__ uint32_t wn[TAIL_WARPS], win_s[TAIL_WARPS], wout_s[TAIL_WARPS];
     __shared__ int s_nflag;
     __shared__ unsigned long long s_chunk, s_prefix;
+    __shared__ uint32_t s_fpage[TAIL_CHUNK];   // list mode: the chunk's flagged pages
+    __shared__ uint32_t s_mred[TAIL_WARPS];
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     unsigned long long *ticket = tail;
     volatile unsigned long long *word = tail + 1;
-    // the first ticket and the list length are fetched while the ranges are staged
+    // the first ticket and the page marks are fetched while the ranges are staged
     if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1ull);
-    const uint64_t nentries = list ? (uint64_t)*nlist : u.npages;
+    const uint32_t G = list ? (uint32_t)((u.npages + 4 * TAIL_THREADS - 1) / (4 * TAIL_THREADS)) * 4 : 0u;
+    uint32_t mw[4] = {0u, 0u, 0u, 0u};   // list mode: bit 32 k + b = page G i + 32 k + b flagged
+    if (list) {
+        const uint64_t p0 = (uint64_t)threadIdx.x * G;
+#pragma unroll
+        for (uint32_t k = 0; k < 128; k += 4) {
+            const uint64_t p = p0 + k;
+            if (k < G && p < u.npages) {
+                uint32_t m;
+                if (p + 4 <= u.npages) {   // 16-byte aligned: page_hits is, and p is a multiple of 4
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(page_hits + p));
+                    m = (v.x != 0u) | (v.y != 0u) << 1 | (v.z != 0u) << 2 | (v.w != 0u) << 3;
+                } else {
+                    m = 0;
+                    for (uint32_t d = 0; p + d < u.npages; ++d) m |= (uint32_t)(page_hits[p + d] != 0u) << d;
+                }
+                mw[k >> 5] |= m << (k & 31);
+            }
+        }
+    }
     const Range *rg = stage_ranges(ca, srg);
     __syncthreads();   // (stage_ranges has none when the ranges stay in global memory)
+    uint64_t nentries = u.npages;
+    uint32_t mpre = 0, mcnt = 0;   // list mode: flagged pages before this thread's, and its own
+    if (list) {
+        mcnt = __popc(mw[0]) + __popc(mw[1]) + __popc(mw[2]) + __popc(mw[3]);
+        uint32_t inc = mcnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        if (lane == 31) s_mred[warp] = inc;
+        __syncthreads();
+        uint32_t before = 0, all = 0;
+        for (int w = 0; w < TAIL_WARPS; ++w) {
+            if (w < warp) before += s_mred[w];
+            all += s_mred[w];
+        }
+        mpre = before + inc - mcnt;
+        nentries = all;
+    }
     if (list) {   // spread the flagged pages over the grid: at most TAIL_CHUNK per chunk
         uint64_t cp = (nentries + gridDim.x - 1) / gridDim.x;
         cpages = (uint32_t)(cp < 1 ? 1 : cp > (uint64_t)TAIL_CHUNK ? TAIL_CHUNK : cp);
@@ -305,11 +293,26 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
         if (c >= nchunks) break;
         const uint64_t e0 = c * cpages;
         const uint64_t e1 = e0 + cpages < nentries ? e0 + cpages : nentries;
+        if (list) {   // the chunk's flagged pages, from the threads whose bits hold them
+            if (mcnt && mpre < e1 && mpre + mcnt > e0) {
+                uint32_t r = mpre;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t x = mw[k];
+                    while (x) {
+                        const uint32_t b = __ffs(x) - 1;
+                        x &= x - 1;
+                        if (r >= e0 && r < e1) s_fpage[r - e0] = G * threadIdx.x + 32u * k + b;
+                        ++r;
+                    }
+                }
+            }
+            __syncthreads();
+        }
         if (warp == 0) {   // the flagged pages and their word offsets in the chunk's sequence
             const uint64_t e = e0 + lane;
-            const unsigned long long ent = (list && e < e1) ? list[e] : 0ull;
-            const uint64_t p = e < e1 ? (list ? ent >> 32 : e) : 0;
-            const uint32_t r = e < e1 ? (list ? (uint32_t)ent : page_hits[p]) : 0u;
+            const uint64_t p = e < e1 ? (list ? (uint64_t)s_fpage[lane] : e) : 0;
+            const uint32_t r = e < e1 ? page_hits[p] : 0u;
             const uint64_t nw = r ? page_span(u, p, (int)r - 1).nwords : 0;
             const uint32_t fm = __ballot_sync(0xffffffffu, r != 0);
             uint64_t inc = nw;
@@ -405,9 +408,8 @@ static uint32_t tail_chunk_pages(uint64_t npages, int sms) {
     return (uint32_t)cp;
 }
 
-// Snapshots of up to this many pages use list mode (the flagged pages listed
-// in page order by one CTA first).
-constexpr uint64_t TAIL_LIST_MAX = 1ull << 16;
+// Snapshots of up to this many pages use list mode (at most 128 pages per thread).
+constexpr uint64_t TAIL_LIST_MAX = 128ull * TAIL_THREADS;
 
 uint64_t census_tail_words(uint64_t npages, int sms) {
     if (npages <= TAIL_LIST_MAX) return 1 + npages;
@@ -416,27 +418,22 @@ uint64_t census_tail_words(uint64_t npages, int sms) {
 }
 
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
-                               unsigned long long *list, kc_hit *hits, uint64_t cap, uint64_t *counts,
-                               uint32_t *status, int sms, uint32_t spin_limit, cudaStream_t st) {
+                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, int sms,
+                               uint32_t spin_limit, cudaStream_t st) {
     if (pg.npages == 0) return cudaSuccess;
     if (spin_limit == 0) spin_limit = LB_SPIN_LIMIT;
     const uint64_t maxb = (uint64_t)sms * 2;
     if (pg.npages <= TAIL_LIST_MAX) {
-        uint32_t *nlist = reinterpret_cast<uint32_t *>(list + pg.npages);
-        census_flag_list_kernel<<<1, FLAG_THREADS, 0, st>>>(page_hits, pg.npages, list, nlist);
-        count_launches(1);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        census_tail_kernel<<<(unsigned)maxb, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, pg.npages, 1, list, nlist,
+        census_tail_kernel<<<(unsigned)maxb, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, pg.npages, 1, true,
                                                                     cap ? hits : nullptr, cap, counts, status,
                                                                     spin_limit);
     } else {
         const uint32_t cp = tail_chunk_pages(pg.npages, sms);
         const uint64_t nchunks = (pg.npages + cp - 1) / cp;
         const uint64_t blocks = nchunks < maxb ? nchunks : maxb;
-        census_tail_kernel<<<(unsigned)blocks, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, nchunks, cp, nullptr,
-                                                                      nullptr, cap ? hits : nullptr, cap, counts,
-                                                                      status, spin_limit);
+        census_tail_kernel<<<(unsigned)blocks, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, nchunks, cp, false,
+                                                                      cap ? hits : nullptr, cap, counts, status,
+                                                                      spin_limit);
     }
     count_launches(1);
     return cudaGetLastError();

@@ -659,18 +659,16 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
     const DigestShape shape = pick_digest_shape(c, page_bytes, P);
     uint32_t *page_hits = nullptr;
     unsigned long long *tail = nullptr;
-    unsigned long long *list = nullptr;
     DigestAux aux;
     uint32_t spin_limit = 0;
     if (census) {
-        // page_hits[P] | census tail: ticket + one word per chunk | list of flagged pages + count
+        // page_hits[P] | census tail: ticket + one word per chunk
         const uint64_t nwords = census_tail_words(P, c->sms);
         const uint64_t hb = (P * 4 + 255) & ~255ull, tb = (nwords * 8 + 255) & ~255ull;
         void *scr = nullptr;
-        if ((s = scratch(c, hb + tb + P * 8 + 8, st, &scr)) != KC_OK) return s;
+        if ((s = scratch(c, hb + tb, st, &scr)) != KC_OK) return s;
         page_hits = static_cast<uint32_t *>(scr);
         tail = reinterpret_cast<unsigned long long *>(static_cast<char *>(scr) + hb);
-        list = reinterpret_cast<unsigned long long *>(static_cast<char *>(scr) + hb + tb);
         aux.zero_words = tail;
         aux.nzero = nwords;
         if (c->stall_census_spins) {   // one-shot test hook: chunk 0 is never taken
@@ -693,7 +691,7 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
                  "digest launch");
     }
     if (census)
-        KC_CHECK(c, launch_census_tail(pg, t->ca, page_hits, tail, list, d_hits, cap, d_counts, status_word(c), c->sms,
+        KC_CHECK(c, launch_census_tail(pg, t->ca, page_hits, tail, d_hits, cap, d_counts, status_word(c), c->sms,
                                        spin_limit, st),
                  "census tail");
     touch(c, t, st);

@@ -215,6 +215,34 @@ def test_scan_sparse_pointers(ctx, page, n_ptr):
     assert int(r["counts"][0]) + int(r["counts"][1]) == len(keep)
 
 
+def test_scan_list_mode_several_rounds(ctx):
+    """Up to 65536 pages the census tail numbers the flagged pages itself and
+    deals them out 1 to 32 per chunk; with more flagged pages than the grid
+    takes in one round (12,289 pages, about 96% of them holding one of 40,000
+    planted pointers) CTAs take further chunks by ticket.  Hits, counts and
+    truncation as the oracle's."""
+    MiB = W.MiB
+    sizes = [20 * MiB + 8, 28 * MiB - 40]
+    layout = W.Snapshot("list-rounds", 4096, sizes, dtypes=[kc.RAW] * len(sizes))
+    snap, dev = G.device_snapshot(layout, _sparse_pointer_fill, 9, n_ptr=40000)
+    npages = sum(-(-s // 4096) for s in sizes)
+    assert 304 * 32 < npages <= 65536
+    win = W.default_window(snap.bases, snap.sizes)
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert rc == 0 and nin + nout > 36000
+    hit_pages = {(h[0], h[1] // 4096) for h in G.hits_tuples(ohits)}
+    assert len(hit_pages) > 304 * 32
+    st, r = G.run_scan(ctx, snap, dev, win, cap=nin + nout)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][: nin + nout]) == G.hits_tuples(ohits)
+    cap = 4321
+    st, r = G.run_scan(ctx, snap, dev, win, cap=cap)
+    assert ctx.sync() == kc.ETRUNC
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][:cap]) == G.hits_tuples(ohits[:cap])
+
+
 def test_scan_page_mode_above_list_limit(ctx):
     """More than 65536 pages: the fused scan's census tail takes chunks of
     consecutive pages (page mode) instead of the list of flagged pages; hits,
