@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
                                                                     kc_hit *__restrict__ hits, uint64_t cap,
                                                                     uint64_t *__restrict__ counts,
                                                                     uint32_t *__restrict__ status,
+                                                                    uint32_t *__restrict__ task_ctr,
                                                                     uint32_t spin_limit) {
     __shared__ Range srg[SMEM_RANGES];
     __shared__ kc_hit stash[TAIL_WARPS][TAIL_STASH];
@@ -231,8 +232,15 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
     const uint32_t lane = lane_id();
     unsigned long long *ticket = tail;
     volatile unsigned long long *word = tail + 1;
-    // the first ticket and the page marks are fetched while the ranges are staged
+    // The ranges are inputs of the call, ready before the digest kernel
+    // started: stage them while it finishes.  Everything after the wait reads
+    // what the digest wrote (page marks, zeroed ticket, chunk words and
+    // counts); the digest's task counter is then free and is reset here for
+    // the next call.
+    const Range *rg = stage_ranges(ca, srg);
+    grid_dep_wait();
     if (threadIdx.x == 0) s_chunk = atomicAdd(ticket, 1ull);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *task_ctr = 0u;
     const uint32_t G = list ? (uint32_t)((u.npages + 4 * TAIL_THREADS - 1) / (4 * TAIL_THREADS)) * 4 : 0u;
     uint32_t mw[4] = {0u, 0u, 0u, 0u};   // list mode: bit 32 k + b = page G i + 32 k + b flagged
     if (list) {
@@ -253,8 +261,7 @@ __global__ void __launch_bounds__(TAIL_THREADS, 2) census_tail_kernel(Pages u, C
             }
         }
     }
-    const Range *rg = stage_ranges(ca, srg);
-    __syncthreads();   // (stage_ranges has none when the ranges stay in global memory)
+    __syncthreads();   // the first ticket
     uint64_t nentries = u.npages;
     uint32_t mpre = 0, mcnt = 0;   // list mode: flagged pages before this thread's, and its own
     if (list) {
@@ -418,25 +425,34 @@ uint64_t census_tail_words(uint64_t npages, int sms) {
 }
 
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
-                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, int sms,
-                               uint32_t spin_limit, cudaStream_t st) {
-    if (pg.npages == 0) return cudaSuccess;
+                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, uint32_t *task_ctr,
+                               int sms, uint32_t spin_limit, cudaStream_t st) {
     if (spin_limit == 0) spin_limit = LB_SPIN_LIMIT;
     const uint64_t maxb = (uint64_t)sms * 2;
-    if (pg.npages <= TAIL_LIST_MAX) {
-        census_tail_kernel<<<(unsigned)maxb, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, pg.npages, 1, true,
-                                                                    cap ? hits : nullptr, cap, counts, status,
-                                                                    spin_limit);
-    } else {
-        const uint32_t cp = tail_chunk_pages(pg.npages, sms);
-        const uint64_t nchunks = (pg.npages + cp - 1) / cp;
-        const uint64_t blocks = nchunks < maxb ? nchunks : maxb;
-        census_tail_kernel<<<(unsigned)blocks, TAIL_THREADS, 0, st>>>(pg, ca, page_hits, tail, nchunks, cp, false,
-                                                                      cap ? hits : nullptr, cap, counts, status,
-                                                                      spin_limit);
+    const bool list = pg.npages <= TAIL_LIST_MAX;
+    uint64_t nchunks = pg.npages, blocks = maxb;
+    uint32_t cp = 1;
+    if (!list) {
+        cp = tail_chunk_pages(pg.npages, sms);
+        nchunks = (pg.npages + cp - 1) / cp;
+        blocks = nchunks < maxb ? nchunks : maxb;
     }
+    if (blocks == 0) blocks = 1;   // no pages: one CTA still resets the task counter
+    // programmatic dependent launch after the digest kernel (which triggers it early)
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(TAIL_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, census_tail_kernel, pg, ca, (const uint32_t *)page_hits, tail, nchunks,
+                                       cp, list, cap ? hits : nullptr, cap, counts, status, task_ctr, spin_limit);
     count_launches(1);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // ---- census: standalone count pass ---------------------------------------------------

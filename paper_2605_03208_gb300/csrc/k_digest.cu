@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(64 * DG_MAX_HASH_WARPS)
         mbar_fence_init();
     }
     __syncthreads();
+    // the census tail (next on the stream) may be scheduled now: its CTAs
+    // take the SMs this grid leaves and wait for its completion themselves
+    grid_dep_launch();
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
 

@@ -683,17 +683,25 @@ static kc_status digest_impl(kc_ctx *c, const kc_buf *allocs, int n, uint32_t pa
         aux.pf_dst = d_page_first;
         aux.npf = (uint64_t)n + 1;
     }
-    KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
+    // The task counter is zero between calls (zeroed with the context; each
+    // call that counts tasks on it sets it back to zero behind its kernel):
+    // here the census tail does, else a memset after the digest.
     {
         Trace tr(c, st);
         KC_CHECK(c, launch_digest(pg, census ? &t->ca : nullptr, d_hash, d_zero, page_hits, task_counter(c),
                                   status_word(c), shape, aux, st),
                  "digest launch");
     }
-    if (census)
-        KC_CHECK(c, launch_census_tail(pg, t->ca, page_hits, tail, d_hits, cap, d_counts, status_word(c), c->sms,
-                                       spin_limit, st),
-                 "census tail");
+    if (census) {
+        const cudaError_t e = launch_census_tail(pg, t->ca, page_hits, tail, d_hits, cap, d_counts, status_word(c),
+                                                 task_counter(c), c->sms, spin_limit, st);
+        if (e != cudaSuccess) {
+            cudaMemsetAsync(task_counter(c), 0, 4, st);
+            return cuda_fail(c, e, "census tail");
+        }
+    } else {
+        KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
+    }
     touch(c, t, st);
     return lost_status(c, t);
 }
@@ -995,13 +1003,14 @@ KC_API kc_status kc_batch_run(kc_ctx *c, const kc_job *jobs, int njobs, uint32_t
     DigestShape shape = pick_batch_shape(c, page_bytes, t->items * 8, t->fused);
     shape.lanes = 1;
     shape.ctas = (int)std::min<uint64_t>((uint64_t)shape.ctas, std::max<uint64_t>(1, t->items));
-    KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
     {
         Trace tr(c, st);
         KC_CHECK(c, launch_batch(t->jobs(), njobs, t->left(), t->work(), t->nranges, t->items, page_bytes, shape,
                                  t->fused, atol, rtol, task_counter(c), c->sms, st),
                  "batch launch");
     }
+    // back to zero for the next call that counts tasks on it
+    KC_CHECK(c, cudaMemsetAsync(task_counter(c), 0, 4, st), "task counter clear");
     touch(c, t, st);
     return t->any_lost ? fail(c, KC_EBUF, "one or more jobs were marked lost") : KC_OK;
 }

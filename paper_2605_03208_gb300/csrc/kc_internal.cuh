@@ -137,14 +137,17 @@ struct DigestAux {
 cudaError_t launch_digest(const Pages &pg, const CensusArgs *census, uint64_t *hash, uint8_t *zero,
                           uint32_t *page_hits, uint32_t *task_ctr, uint32_t *status, const DigestShape &shape,
                           const DigestAux &aux, cudaStream_t st);
-// Census of the fused scan after the digest kernel.  tail:
-// census_tail_words(P, sms) words zeroed by the digest kernel.
+// Census of the fused scan, launched right after the digest kernel on the
+// same stream (programmatic dependent launch: it waits for the digest inside
+// the kernel).  tail: census_tail_words(P, sms) words zeroed by the digest
+// kernel; task_ctr: the digest's task counter, reset to zero for the next
+// call (also when P = 0).
 uint64_t census_tail_words(uint64_t npages, int sms);
 // spin_limit: polls each look-back wait makes before it gives up (0 = the
 // built-in limit of a few seconds).
 cudaError_t launch_census_tail(const Pages &pg, const CensusArgs &ca, uint32_t *page_hits, unsigned long long *tail,
-                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, int sms,
-                               uint32_t spin_limit, cudaStream_t st);
+                               kc_hit *hits, uint64_t cap, uint64_t *counts, uint32_t *status, uint32_t *task_ctr,
+                               int sms, uint32_t spin_limit, cudaStream_t st);
 cudaError_t launch_census_count(const Pages &units, const CensusArgs &ca, uint32_t *unit_hits,
                                 uint64_t *counts, int sms, cudaStream_t st);
 cudaError_t launch_census_write(const Pages &units, const CensusArgs &ca,

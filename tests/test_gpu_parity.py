@@ -620,17 +620,42 @@ def test_graph_capture_replays_bit_exact(ctx, tiny):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         step()
-    for t in (h, z, table, arena, nb, counts):
-        t.zero_()
-    for t in targets:
-        t.fill_(0xA5)
-    g.replay()
-    torch.cuda.synchronize()
-    assert ctx.sync() == kc.OK
     oh, oz, _ = oracle.digest(snap.regions, S)
-    assert np.array_equal(G.to_np(h).view(np.uint64), oh) and np.array_equal(G.to_np(z), oz)
     ot = oracle.dedup(snap.regions, S, oh, oz)
-    assert int(G.to_np(nb).view(np.uint64)[0]) == ot["n_blobs"]
-    assert np.array_equal(G.to_np(table).view(kc.PAGE_DTYPE)["blob"], ot["blob"])
-    for tg, r in zip(targets, snap.regions):
-        assert np.array_equal(G.to_np(tg), r)
+    ohits, nin, nout, _ = oracle.census(snap.regions, snap.bases, *win)
+    for _ in range(3):   # each replay leaves the state the next one starts from
+        for t in (h, z, table, arena, nb, counts):
+            t.zero_()
+        for t in targets:
+            t.fill_(0xA5)
+        g.replay()
+        torch.cuda.synchronize()
+        assert ctx.sync() == kc.OK
+        assert np.array_equal(G.to_np(h).view(np.uint64), oh) and np.array_equal(G.to_np(z), oz)
+        assert tuple(G.to_np(counts).view(np.uint64)) == (nin, nout)
+        got = G.to_np(hits).view(kc.HIT_DTYPE)[: nin + nout]
+        assert G.hits_tuples(got) == G.hits_tuples(ohits)
+        assert int(G.to_np(nb).view(np.uint64)[0]) == ot["n_blobs"]
+        assert np.array_equal(G.to_np(table).view(kc.PAGE_DTYPE)["blob"], ot["blob"])
+        for tg, r in zip(targets, snap.regions):
+            assert np.array_equal(G.to_np(tg), r)
+
+
+def test_digest_and_scan_interleave_on_one_context(ctx, tiny):
+    """kc_digest and kc_scan take tasks from one counter of the context,
+    each leaving it at zero behind its kernels: any order of the two gives
+    the oracle's digests, and the scan the oracle's census."""
+    snap, dev = tiny
+    win = W.default_window(snap.bases, snap.sizes)
+    oh, oz, _ = oracle.digest(snap.regions, snap.page_bytes)
+    ohits, nin, nout, _ = oracle.census(snap.regions, snap.bases, *win)
+    for op in ["scan", "digest", "digest", "scan", "scan", "digest", "scan"]:
+        if op == "scan":
+            st, r = G.run_scan(ctx, snap, dev, win)
+            h, z = r["hash"], r["zero"]
+            assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+            assert G.hits_tuples(r["hits"][: nin + nout]) == G.hits_tuples(ohits)
+        else:
+            st, h, z, _ = G.run_digest(ctx, snap, dev)
+        assert st == kc.OK and ctx.sync() == kc.OK
+        assert np.array_equal(h, oh) and np.array_equal(z, oz)
