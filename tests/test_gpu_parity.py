@@ -306,6 +306,65 @@ def test_census_standalone(ctx, tiny):
     assert G.hits_tuples(hits[: nin + nout]) == G.hits_tuples(ohits)
 
 
+def _edge_fill(snap, bases, seed=0):
+    """Random bytes, with words at and next to every region's first and last
+    byte, at the quarter points of the gaps between regions, and at the
+    boundaries of 2^16 equal buckets over the regions' hull (around each
+    region's ends), planted as 8-byte words in the two largest regions."""
+    rng = np.random.default_rng(seed + 3)
+    snap.bases = [int(b) for b in bases]
+    lo = min(snap.bases)
+    hi = max(b + s for b, s in zip(snap.bases, snap.sizes))
+    shift = 0
+    while ((hi - lo - 1) >> shift) >= 1 << 16:
+        shift += 1
+    vals = []
+    for b, s in zip(snap.bases, snap.sizes):
+        vals += [b - 8, b - 1, b, b + 1, b + s - 8, b + s - 1, b + s, b + s + 1, b + s + 8]
+        for e in (b, b + s):
+            k = (e - lo) >> shift
+            for kk in (k - 1, k, k + 1, k + 2):
+                x = lo + (kk << shift)
+                vals += [x - 1, x, x + 1]
+    order = sorted(zip(snap.bases, snap.sizes))
+    for (b0, s0), (b1, _) in zip(order, order[1:]):
+        if b1 > b0 + s0:
+            vals += [b0 + s0 + (b1 - b0 - s0) * q // 4 for q in (1, 2, 3)]
+    vals += [lo - 1, hi, hi + 1, 0, 2 ** 64 - 1]
+    vals = np.array([v % 2 ** 64 for v in vals], dtype=np.uint64)
+    regions = [rng.integers(0, 256, s, dtype=np.uint8) for s in snap.sizes]
+    big = sorted(range(len(snap.sizes)), key=lambda i: -snap.sizes[i])[:2]
+    for i in big:
+        at = rng.choice(snap.sizes[i] // 8, size=len(vals), replace=False) * 8
+        for v, o in zip(vals.tolist(), at.tolist()):
+            regions[i][o:o + 8] = np.array([v], np.uint64).view(np.uint8)
+    snap.regions = regions
+    snap.truth = {"values": len(vals)}
+    return snap
+
+
+@pytest.mark.parametrize("page", [4096, 65536])
+def test_census_edges_and_gaps(ctx, page):
+    """Every planted word classified as the oracle does -- inside, outside or
+    no hit -- at region edges, in the gaps between regions and on the
+    classifier's bucket boundaries: fused scan and standalone census."""
+    MiB, KiB = W.MiB, 1024
+    sizes = [4096, 2 * MiB + 8, 64 * KiB, 20 * MiB, 4096 + 8, 3 * MiB, 40]
+    layout = W.Snapshot("edges", page, sizes, dtypes=[kc.RAW] * len(sizes))
+    snap, dev = G.device_snapshot(layout, _edge_fill, 4)
+    win = W.default_window(snap.bases, snap.sizes)
+    ohits, nin, nout, rc = oracle.census(snap.regions, snap.bases, *win)
+    assert rc == 0 and nin > 0 and nout > 0
+    st, r = G.run_scan(ctx, snap, dev, win, page_bytes=page)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    assert (int(r["counts"][0]), int(r["counts"][1])) == (nin, nout)
+    assert G.hits_tuples(r["hits"][: nin + nout]) == G.hits_tuples(ohits)
+    st, hits, counts = G.run_census(ctx, snap, dev, win)
+    assert st == kc.OK and ctx.sync() == kc.OK
+    assert (int(counts[0]), int(counts[1])) == (nin, nout)
+    assert G.hits_tuples(hits[: nin + nout]) == G.hits_tuples(ohits)
+
+
 def test_census_dense_pointers_and_truncation(ctx):
     layout = W.tiny_layout(3, n=12, total=6 * W.MiB)
     snap, dev = G.device_snapshot(layout, W.tiny_fill, 3, p_ptr=0.6, p_zero=0.1)
