@@ -86,8 +86,12 @@ __device__ __forceinline__ UnitSpan unit_span(const Pages &u, uint64_t unit) {
 // ---- census tail of the fused scan: one kernel, decoupled look-back ---------------
 //
 // After the digest kernel, page_hits[p] is the region index + 1 for pages
-// holding a word that passed the pre-filter and 0 otherwise.  CTAs take
-// chunks of TAIL_CHUNK pages in ticket order.  For each chunk: (A) the
+// holding a word that passed the pre-filter and 0 otherwise.  The kernel is
+// launched right behind the digest as a programmatic dependent: its CTAs
+// stage the range table while the digest finishes and wait for it before
+// reading anything it wrote.  CTAs take chunks in ticket order -- up to
+// TAIL_CHUNK flagged pages each (list mode), or runs of consecutive pages
+// above TAIL_LIST_MAX pages (page mode).  For each chunk: (A) the
 // words of its flagged pages, taken as one sequence in page order, are split
 // evenly between the CTA's warps; each warp classifies its run, counts its
 // hits and keeps the first TAIL_STASH of them, in word order, in shared
@@ -106,6 +110,7 @@ constexpr int TAIL_THREADS = 512;
 constexpr int TAIL_WARPS = TAIL_THREADS / 32;
 constexpr int TAIL_CHUNK = 32;     // most pages per chunk (one warp lane each when listing them)
 constexpr int TAIL_STASH = 128;    // hits a warp keeps in shared memory (48 KB per CTA)
+constexpr uint64_t TAIL_LIST_MAX = 128ull * TAIL_THREADS;   // list mode up to here (128 page marks per thread)
 constexpr unsigned long long LB_AGG = 1ull << 62;      // chunk word: total of the chunk
 constexpr unsigned long long LB_PREFIX = 2ull << 62;   // chunk word: inclusive prefix
 constexpr unsigned long long LB_VALUE = (1ull << 62) - 1;
@@ -414,9 +419,6 @@ static uint32_t tail_chunk_pages(uint64_t npages, int sms) {
     if (cp > (uint64_t)TAIL_CHUNK) cp = TAIL_CHUNK;
     return (uint32_t)cp;
 }
-
-// Snapshots of up to this many pages use list mode (at most 128 pages per thread).
-constexpr uint64_t TAIL_LIST_MAX = 128ull * TAIL_THREADS;
 
 uint64_t census_tail_words(uint64_t npages, int sms) {
     if (npages <= TAIL_LIST_MAX) return 1 + npages;
