@@ -139,12 +139,29 @@ __device__ __forceinline__ uint32_t elem_of(uint32_t w, int j) {
     return (w >> (8 * j)) & 0xffu;
 }
 
+// NaN elements of a word: the high bit of each element's slot set by one
+// carry per element ((x & mag) + (mag - inf)) -- an element is NaN iff its
+// magnitude exceeds the infinity pattern -- then counted.
+template <int DT>
+__device__ __forceinline__ uint32_t nan_bits(uint32_t w) {
+    if (DT == KC_F32) return ((w & 0x7fffffffu) + 0x007fffffu) & 0x80000000u;
+    if (DT == KC_BF16) return ((w & 0x7fff7fffu) + 0x007f007fu) & 0x80008000u;
+    if (DT == KC_F16) return ((w & 0x7fff7fffu) + 0x03ff03ffu) & 0x80008000u;
+    return 0u;
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t vec_nans(const uint4 &v) {
+    if (!(DT == KC_F32 || DT == KC_F16 || DT == KC_BF16)) return 0u;
+    const uint32_t a = nan_bits<DT>(v.x), b = nan_bits<DT>(v.y), c = nan_bits<DT>(v.z), d = nan_bits<DT>(v.w);
+    if ((a | b | c | d) == 0u) return 0u;
+    return __popc(a) + __popc(b) + __popc(c) + __popc(d);
+}
+
 // NaNs in a word whose got and want bits are identical.
 template <int DT>
 __device__ __forceinline__ uint32_t word_nans(uint32_t w) {
-    if (DT == KC_F32) return bits_nan<DT>(w);
-    if (DT == KC_BF16 || DT == KC_F16) return bits_nan<DT>(w & 0xffffu) + bits_nan<DT>(w >> 16);
-    return 0;
+    return __popc(nan_bits<DT>(w));
 }
 
 template <int DT>
@@ -175,12 +192,9 @@ __device__ __forceinline__ void cmp_vec(uint4 g, uint4 w, unsigned long long fir
                                         double rtol, CmpAcc &acc, const SlowQ &q) {
     constexpr int per = 4 / esize<DT>();
     if (g.x == w.x && g.y == w.y && g.z == w.z && g.w == w.w) {
-        if (DT == KC_F32 || DT == KC_F16 || DT == KC_BF16) {
-            const uint32_t n = word_nans<DT>(g.x) + word_nans<DT>(g.y) + word_nans<DT>(g.z) +
-                               word_nans<DT>(g.w);
-            acc.nan_g += n;
-            acc.nan_w += n;
-        }
+        const uint32_t n = vec_nans<DT>(g);
+        acc.nan_g += n;
+        acc.nan_w += n;
         return;
     }
     cmp_word<DT>(g.x, w.x, first_elem, atol, rtol, acc, q);
@@ -275,25 +289,6 @@ __device__ __forceinline__ void cmp_drain_any(int dt, const SlowQ &q, uint32_t m
 // few elements that can hold the maxima (below).
 
 __device__ __forceinline__ CmpAcc cmp_acc_zero() { return CmpAcc{0ull, ~0ull, 0ull, 0ull, 0ull, 0.0, 0.0}; }
-
-// NaN elements of a word: the high bit of each element's slot set by one
-// carry per element ((x & mag) + (mag - inf)) -- an element is NaN iff its
-// magnitude exceeds the infinity pattern -- then counted.
-template <int DT>
-__device__ __forceinline__ uint32_t nan_bits(uint32_t w) {
-    if (DT == KC_F32) return ((w & 0x7fffffffu) + 0x007fffffu) & 0x80000000u;
-    if (DT == KC_BF16) return ((w & 0x7fff7fffu) + 0x007f007fu) & 0x80008000u;
-    if (DT == KC_F16) return ((w & 0x7fff7fffu) + 0x03ff03ffu) & 0x80008000u;
-    return 0u;
-}
-
-template <int DT>
-__device__ __forceinline__ uint32_t vec_nans(const uint4 &v) {
-    if (!(DT == KC_F32 || DT == KC_F16 || DT == KC_BF16)) return 0u;
-    const uint32_t a = nan_bits<DT>(v.x), b = nan_bits<DT>(v.y), c = nan_bits<DT>(v.z), d = nan_bits<DT>(v.w);
-    if ((a | b | c | d) == 0u) return 0u;
-    return __popc(a) + __popc(b) + __popc(c) + __popc(d);
-}
 
 struct VecItem {        // a queued vector: its index in the pair and both sides' bits
     unsigned long long v;
