@@ -73,7 +73,9 @@ __device__ __forceinline__ void batch_item_done(const BatchJob &J, uint32_t *lef
 
 // Stage st's chunk c of the 8 pages: page r's got bytes at gslot(r), want
 // bytes one half-stage later; br = that page's bytes in this chunk.
-template <int DT>
+// With a compile-time chunk of at most 512 bytes every lane takes at most one
+// vector of each page: no loop.
+template <int DT, int CHUNK>
 __device__ __forceinline__ void fused_cmp_stage(const uint8_t *stage, size_t slot_stride, uint32_t b, uint64_t off0,
                                                 uint32_t log2page, uint32_t chunk_off, double atol, double rtol,
                                                 CmpAcc &acc, const SlowQ &q) {
@@ -85,9 +87,16 @@ __device__ __forceinline__ void fused_cmp_stage(const uint8_t *stage, size_t slo
         const uint8_t *gs = stage + (size_t)r * slot_stride;
         const uint8_t *ws = gs + BATCH_PPW * slot_stride;
         const uint64_t byte0 = off0 + ((uint64_t)r << log2page) + chunk_off;
-        for (uint32_t i = lane; i < br / 16; i += 32)
-            cmp_vec<DT>(*reinterpret_cast<const uint4 *>(gs + 16 * i), *reinterpret_cast<const uint4 *>(ws + 16 * i),
-                        (byte0 + 16 * i) / ES, atol, rtol, acc, q);
+        if (CHUNK > 0 && CHUNK <= 512) {
+            if (lane < br / 16)
+                cmp_vec<DT>(*reinterpret_cast<const uint4 *>(gs + 16 * lane),
+                            *reinterpret_cast<const uint4 *>(ws + 16 * lane), (byte0 + 16 * lane) / ES, atol, rtol,
+                            acc, q);
+        } else {
+            for (uint32_t i = lane; i < br / 16; i += 32)
+                cmp_vec<DT>(*reinterpret_cast<const uint4 *>(gs + 16 * i),
+                            *reinterpret_cast<const uint4 *>(ws + 16 * i), (byte0 + 16 * i) / ES, atol, rtol, acc, q);
+        }
     }
 }
 
@@ -170,11 +179,11 @@ __device__ __forceinline__ PageDigest fused_pages(uint8_t *ring, int stages, int
         }
         hash_chunk<false, 1, CHUNK>(L, stage + qs * slot_stride + 8 * j, b, none);
         switch (J.dtype) {
-        case KC_F32: fused_cmp_stage<KC_F32>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
-        case KC_F16: fused_cmp_stage<KC_F16>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
-        case KC_BF16: fused_cmp_stage<KC_BF16>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
-        case KC_I32: fused_cmp_stage<KC_I32>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
-        default: fused_cmp_stage<KC_U8>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
+        case KC_F32: fused_cmp_stage<KC_F32, CHUNK>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
+        case KC_F16: fused_cmp_stage<KC_F16, CHUNK>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
+        case KC_BF16: fused_cmp_stage<KC_BF16, CHUNK>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
+        case KC_I32: fused_cmp_stage<KC_I32, CHUNK>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
+        default: fused_cmp_stage<KC_U8, CHUNK>(stage, slot_stride, b, off0, log2page, c * chunk, atol, rtol, acc, q); break;
         }
         __syncwarp();   // the stage is free for the next refill
     }
