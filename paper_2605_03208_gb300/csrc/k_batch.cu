@@ -157,9 +157,17 @@ __device__ __forceinline__ PageDigest fused_pages(uint8_t *ring, int stages, int
             uint8_t *dst = ring + (c % stages) * stage_stride + qs * slot_stride;
             const uint8_t *from = src + (size_t)c * chunk;
             const uint8_t *wfrom = wsrc + (size_t)c * chunk;
-            for (uint32_t o = 16 * j; o < b; o += 64) {
-                cp_async16(dst + o, from + o);
-                cp_async16(dst + BATCH_PPW * slot_stride + o, wfrom + o);
+            if (CHUNK && b == (uint32_t)CHUNK) {   // a full chunk of compile-time size: unrolled
+#pragma unroll
+                for (int o = 16 * j; o < (CHUNK ? CHUNK : 64); o += 64) {
+                    cp_async16(dst + o, from + o);
+                    cp_async16(dst + BATCH_PPW * slot_stride + o, wfrom + o);
+                }
+            } else {
+                for (uint32_t o = 16 * j; o < b; o += 64) {
+                    cp_async16(dst + o, from + o);
+                    cp_async16(dst + BATCH_PPW * slot_stride + o, wfrom + o);
+                }
             }
         }
         cp_async_commit();
